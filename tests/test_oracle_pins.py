@@ -1,0 +1,337 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test ties the oracle to something other than itself: the numbers printed
+in Table 1, the closed-form spectrum of the free field, anti-hermiticity of
+Eq. 3, gauge covariance, a dense library solve, and exact reconstruction of
+unitary links. None of them needs a GPU.
+"""
+import numpy as np
+import pytest
+
+import hisq_inputs as gen
+from oracle import hisq_oracle as O
+from conftest import read_golden
+
+LATTICES = [(8, 8, 8, 8), (4, 6, 8, 10)]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def gaussian_full(L, n, seed):
+    rng = np.random.default_rng(seed)
+    shape = (n,) + O.grid_shape(L) + (3,)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2)
+
+
+def coords(L):
+    Lt, Lz, Ly, Lx = O.grid_shape(L)
+    t, z, y, x = np.meshgrid(np.arange(Lt), np.arange(Lz), np.arange(Ly),
+                             np.arange(Lx), indexing="ij")
+    return x, y, z, t
+
+
+def plane_wave(L, k, chi):
+    """e^{i p.x} chi with p_mu = 2 pi k_mu / L_mu (mu < 3), p_t = (2 k_t + 1) pi / Lt."""
+    x, y, z, t = coords(L)
+    p = [2 * np.pi * k[0] / L[0], 2 * np.pi * k[1] / L[1], 2 * np.pi * k[2] / L[2],
+         (2 * k[3] + 1) * np.pi / L[3]]
+    ph = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+    return ph[None, ..., None] * np.asarray(chi)[None, None, None, None, None, :], p
+
+
+def free_s(p, c1, c3, mu_chem=0.0):
+    s = [2 * c1 * np.sin(q) + 2 * c3 * np.sin(3 * q) for q in p[:3]]
+    q = p[3] - 1j * mu_chem
+    s.append(2 * c1 * np.sin(q) + 2 * c3 * np.sin(3 * q))
+    return s
+
+
+# ---------------------------------------------------------------------------
+# Table 1 and the intensity statements of Sec. 1 / Sec. 3 (golden fixtures)
+# ---------------------------------------------------------------------------
+
+def test_table1_arithmetic_intensity():
+    rows = read_golden("table1_arithmetic_intensity.txt")
+    assert len(rows) == 7
+    for n, full, r14 in rows:
+        n = int(n)
+        assert round(O.dslash_intensity(n, 18), 2) == pytest.approx(float(full), abs=1e-9)
+        assert round(O.dslash_intensity(n, 14), 2) == pytest.approx(float(r14), abs=1e-9)
+
+
+def test_intensity_statements():
+    g = {r[0]: [float(v) for v in r[1:]] for r in read_golden("intensity_statements.txt")}
+    limit = O.dslash_flops(1) / ((16 * 6 + 6) * 4)
+    assert abs(limit - g["limit"][0]) <= g["limit"][1]
+    assert abs(O.dslash_intensity(8, 18) / limit - g["frac_n8"][0]) <= g["frac_n8"][1]
+    for f in (18, 14):
+        frac1 = O.dslash_intensity(1, f) / limit
+        assert g["frac_n1_lo"][0] <= frac1 <= g["frac_n1_hi"][0]
+    ratio = O.dslash_intensity(4, 14) / O.dslash_intensity(1, 14)
+    assert abs(ratio - g["ratio_r14_4_over_1"][0]) <= g["ratio_r14_4_over_1"][1]
+
+
+def test_flop_count_by_operation_census():
+    # one complex multiply = 4 mul + 2 add, one complex add = 2 add
+    assert O.MATVEC_FLOPS == 9 * (4 + 2) + 6 * 2
+    assert O.dslash_flops(1) == 1146
+
+
+# ---------------------------------------------------------------------------
+# Geometry: the half-lattice index h = i // 2 within one parity
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", LATTICES)
+def test_half_index_is_lex_over_two(L):
+    x, y, z, t = coords(L)
+    lex = x + L[0] * (y + L[1] * (z + L[2] * t))
+    for p in (0, 1):
+        field = lex.astype(np.complex128)[None, ..., None] * np.ones(3)
+        half = O.to_half(field, L, p)
+        vh = lex.size // 2
+        assert half.shape == (1, vh, 3)
+        h_of = (half[0, :, 0].real.astype(np.int64)) // 2
+        np.testing.assert_array_equal(h_of, np.arange(vh))
+        par = (x + y + z + t) % 2
+        sel = lex[par == p]
+        np.testing.assert_array_equal(np.sort(sel), half[0, :, 0].real.astype(np.int64))
+        back = O.to_full(half, L, p)
+        np.testing.assert_array_equal(back[0][par == p], field[0][par == p])
+        assert np.all(back[0][par != p] == 0)
+
+
+# ---------------------------------------------------------------------------
+# P1: free field. -D^2 acts on plane waves as sum_mu s_mu(p)^2.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", LATTICES)
+@pytest.mark.parametrize("mu_chem", [0.0, 0.3])
+def test_free_field_plane_wave_spectrum(L, mu_chem):
+    c1, c3 = 9.0 / 8.0, -1.0 / 24.0
+    U, N = gen.free_field_links(L, c1, c3)
+    rng = np.random.default_rng(5)
+    for trial in range(4):
+        k = [int(rng.integers(0, L[m])) for m in range(4)]
+        chi = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+        v, p = plane_wave(L, k, chi)
+        lam = sum(s * s for s in free_s(p, c1, c3, mu_chem))
+        Dv = O.dslash(U, N, v, mu_chem)
+        DDv = O.dslash(U, N, Dv, mu_chem)
+        assert rel(-DDv, lam * v) < 1e-12
+
+
+@pytest.mark.parametrize("L", LATTICES)
+def test_free_field_even_odd_eigenvector_and_one_step_cg(L):
+    c1, c3, m = 9.0 / 8.0, -1.0 / 24.0, 0.05
+    U, N = gen.free_field_links(L, c1, c3)
+    k = [1, 2, 0, 1]
+    v, p = plane_wave(L, k, [1.0, 0.5j, -0.25])
+    lam = 4 * m * m + sum(s * s for s in free_s(p, c1, c3)).real
+    ve = O.to_half(v, L, 0)
+    Av = O.apply_Ae(U, N, ve, L, m)
+    assert rel(Av, lam * ve) < 1e-12
+    x, iters = O.cg(lambda q: O.apply_Ae(U, N, q, L, m), ve, tol=1e-12)
+    assert iters[0] == 1
+    assert rel(x, ve / lam) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# P2: anti-hermiticity <w, D v> = -<D w, v>; D(mu)^dag = -D(-mu)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", LATTICES)
+@pytest.mark.parametrize("mu_chem", [0.0, 0.2])
+def test_anti_hermiticity(L, mu_chem):
+    U, N = gen.hisq_links(L, seed=11)
+    v = gaussian_full(L, 2, 1)
+    w = gaussian_full(L, 2, 2)
+    lhs = np.vdot(w, O.dslash(U, N, v, mu_chem))
+    rhs = -np.vdot(O.dslash(U, N, w, -mu_chem), v)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(w) * np.linalg.norm(v) * 10
+
+
+@pytest.mark.parametrize("L", LATTICES)
+def test_parity_blocks_adjoint(L):
+    U, N = gen.hisq_links(L, seed=12)
+    a_e = gen.gaussian_source(L, 2, 3)
+    b_o = gen.gaussian_source(L, 2, 4)
+    lhs = np.vdot(a_e, O.dslash_parity(U, N, b_o, L, 0))      # <a_e, D_eo b_o>
+    rhs = -np.vdot(O.dslash_parity(U, N, a_e, L, 1), b_o)     # -<D_oe a_e, b_o>
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(a_e) * np.linalg.norm(b_o)
+
+
+def test_dslash_is_parity_off_diagonal():
+    L = (4, 6, 8, 10)
+    U, N = gen.hisq_links(L, seed=13)
+    v = gaussian_full(L, 1, 5)
+    ve = O.to_full(O.to_half(v, L, 0), L, 0)
+    Dve = O.dslash(U, N, ve)
+    assert np.all(Dve[:, O.parity_mask(L, 0)] == 0)
+
+
+# ---------------------------------------------------------------------------
+# P3: gauge covariance U -> g U g'^dag, N -> g N g'''^dag, v -> g v
+# ---------------------------------------------------------------------------
+
+def gauge_transform(L, U, N, g):
+    gd = np.conj(np.swapaxes(g, -1, -2))
+    U2 = np.empty_like(U)
+    N2 = np.empty_like(N)
+    for mu in range(4):
+        U2[mu] = g @ U[mu] @ O.shift(gd, mu, +1, 0)
+        N2[mu] = g @ N[mu] @ O.shift(gd, mu, +3, 0)
+    return U2, N2
+
+
+@pytest.mark.parametrize("L", LATTICES)
+@pytest.mark.parametrize("mu_chem", [0.0, 0.25])
+def test_gauge_covariance(L, mu_chem):
+    U, N = gen.hisq_links(L, seed=21)
+    g = gen.random_su3_field(L, seed=22)
+    U2, N2 = gauge_transform(L, U, N, g)
+    v = gaussian_full(L, 2, 7)
+    gv = np.einsum("tzyxij,ntzyxj->ntzyxi", g, v)
+    lhs = O.dslash(U2, N2, gv, mu_chem)
+    rhs = np.einsum("tzyxij,ntzyxj->ntzyxi", g, O.dslash(U, N, v, mu_chem))
+    assert rel(lhs, rhs) < 1e-13
+
+
+def test_gauge_covariance_of_cg_solution():
+    L, m = (4, 4, 4, 6), 0.1
+    U, N = gen.hisq_links(L, seed=23)
+    g = gen.random_su3_field(L, seed=24)
+    U2, N2 = gauge_transform(L, U, N, g)
+    b = gen.z2_source(L, 1, 25)
+    # g restricted to even sites, as a (V_h, 3, 3) stack
+    mask = O.parity_mask(L, 0)
+    g_e = g[mask]
+    x, _ = O.cg(lambda q: O.apply_Ae(U, N, q, L, m), b, tol=1e-13)
+    gb = np.einsum("hij,nhj->nhi", g_e, b)
+    x2, _ = O.cg(lambda q: O.apply_Ae(U2, N2, q, L, m), gb, tol=1e-13)
+    assert rel(x2, np.einsum("hij,nhj->nhi", g_e, x)) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# P4 / P6: dense library solve, hermiticity and positivity of the CG system
+# ---------------------------------------------------------------------------
+
+def test_dense_even_odd_system_matches_library_solve():
+    L, m = (4, 4, 4, 4), 0.05
+    U, N = gen.hisq_links(L, seed=31)
+    vh = 128
+    A = O.dense_matrix(lambda q: O.apply_Ae(U, N, q, L, m), (vh, 3))
+    assert A.shape == (384, 384)
+    assert np.abs(A - A.conj().T).max() < 1e-13
+    ev = np.linalg.eigvalsh(A)
+    assert ev.min() >= 4 * m * m * (1 - 1e-10)
+    # A_e = 4m^2 + D_oe^dag D_oe with D_oe the odd<-even block of the dense D
+    Doe = O.dense_matrix(lambda q: O.dslash_parity(U, N, q, L, 1), (vh, 3))
+    assert np.abs(A - (4 * m * m * np.eye(384) + Doe.conj().T @ Doe)).max() < 1e-12
+    b = gen.z2_source(L, 2, 32)
+    x_lu = np.linalg.solve(A, b.reshape(2, -1).T).T.reshape(b.shape)
+    x_cg, iters = O.cg(lambda q: O.apply_Ae(U, N, q, L, m), b, tol=1e-13)
+    assert rel(x_cg, x_lu) < 1e-10
+    assert np.all(O.true_relative_residual(lambda q: O.apply_Ae(U, N, q, L, m), x_cg, b) < 1e-12)
+
+
+def test_dense_full_lattice_normal_system_with_mu():
+    L, m, mu = (4, 4, 4, 4), 0.1, 0.1
+    U, N = gen.hisq_links(L, seed=33)
+    shape = O.grid_shape(L) + (3,)
+    M = O.dense_matrix(lambda q: O.apply_M(U, N, q, m, mu), shape)
+    Md = O.dense_matrix(lambda q: O.apply_Mdag(U, N, q, m, mu), shape)
+    assert np.abs(Md - M.conj().T).max() < 1e-13          # M^dag is the adjoint of M
+    A = O.dense_matrix(lambda q: O.apply_MdagM(U, N, q, m, mu), shape)
+    assert np.abs(A - M.conj().T @ M).max() < 1e-12
+    rng = np.random.default_rng(34)
+    b = rng.standard_normal((1,) + shape) + 1j * rng.standard_normal((1,) + shape)
+    x_lu = np.linalg.solve(A, b.reshape(1, -1).T).T.reshape(b.shape)
+    x_cg, _ = O.cg(lambda q: O.apply_MdagM(U, N, q, m, mu), b, tol=1e-13)
+    assert rel(x_cg, x_lu) < 1e-9
+
+
+def test_full_lattice_solve_equals_even_odd_at_zero_mu():
+    L, m = (4, 4, 4, 6), 0.1
+    U, N = gen.hisq_links(L, seed=35)
+    b_e = gen.z2_source(L, 1, 36)
+    x_e, _ = O.cg(lambda q: O.apply_Ae(U, N, q, L, m), b_e, tol=1e-13)
+    b_full = O.to_full(b_e, L, 0)
+    x_full, _ = O.cg(lambda q: O.apply_MdagM(U, N, q, m, 0.0), b_full, tol=1e-13)
+    assert rel(O.to_half(x_full, L, 0), x_e) < 1e-10
+    assert np.linalg.norm(O.to_half(x_full, L, 1)) < 1e-10 * np.linalg.norm(x_e)
+
+
+@pytest.mark.parametrize("L", [(8, 8, 8, 8)])
+def test_hermitian_positive_system_random_vectors(L):
+    m = 0.05
+    U, N = gen.hisq_links(L, seed=41)
+    u = gen.gaussian_source(L, 1, 42)
+    v = gen.gaussian_source(L, 1, 43)
+    Au = O.apply_Ae(U, N, u, L, m)
+    Av = O.apply_Ae(U, N, v, L, m)
+    assert abs(np.vdot(u, Av) - np.conj(np.vdot(v, Au))) < 1e-12 * np.linalg.norm(u) * np.linalg.norm(v) * 10
+    assert np.vdot(v, Av).real >= 4 * m * m * np.vdot(v, v).real
+
+
+# ---------------------------------------------------------------------------
+# CG behaviour per rhs
+# ---------------------------------------------------------------------------
+
+def test_cg_per_rhs_freezing_and_zero_source():
+    L, m = (4, 4, 4, 4), 0.05
+    U, N = gen.hisq_links(L, seed=51)
+    b = gen.z2_source(L, 3, 52)
+    b[1] = 0.0
+    x, iters = O.cg(lambda q: O.apply_Ae(U, N, q, L, m), b, tol=1e-11)
+    assert iters[1] == 0 and np.all(x[1] == 0)
+    # per-rhs solutions equal the single-rhs solves
+    for k in (0, 2):
+        xk, _ = O.cg(lambda q: O.apply_Ae(U, N, q, L, m), b[k:k + 1], tol=1e-11)
+        assert rel(x[k], xk[0]) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# P7: link compression round trips and rejection
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", LATTICES)
+def test_r14_round_trip_on_naik_links(L):
+    U, N = gen.hisq_links(L, seed=61)
+    packed = O.compress_r14(N)
+    assert packed.shape == N.shape[:-2] + (14,)
+    back = O.reconstruct_r14(packed)
+    assert np.abs(back - N).max() < 5e-14
+    z = packed[..., 12] + 1j * packed[..., 13]
+    assert np.allclose(np.abs(z), 24.0, rtol=1e-12)     # |z| = 1/|c| for N = c W, W in U(3)
+    # r14 also holds for U(3)-type links after a gauge transform
+    g = gen.random_su3_field(L, seed=62)
+    _, N2 = gauge_transform(L, U, N, g)
+    assert np.abs(O.reconstruct_r14(O.compress_r14(N2)) - N2).max() < 5e-14
+
+
+@pytest.mark.parametrize("L", LATTICES)
+def test_r12_round_trip_on_fat_links(L):
+    U, N = gen.hisq_links(L, seed=63)
+    back = O.reconstruct_r12(O.compress_r12(U), L, 0.9, hop=1)
+    assert np.abs(back - U).max() < 5e-14
+    # Naik links are U(3), not sign * SU(3): r12 must not reproduce them
+    backN = O.reconstruct_r12(O.compress_r12(N), L, 1.0 / 24.0, hop=3)
+    assert np.abs(backN - N).max() > 1e-3
+
+
+def test_reconstruct_rejects_non_unitary():
+    rng = np.random.default_rng(64)
+    m = rng.standard_normal((10, 3, 3)) + 1j * rng.standard_normal((10, 3, 3))
+    back = O.reconstruct_r14(O.compress_r14(m))
+    assert np.abs(back - m).max() > 1e-2
+
+
+def test_link_sign_matches_generator_phases():
+    # sigma in the r12 reconstruction equals the sign folded into the links
+    L = (4, 6, 8, 10)
+    U, _ = gen.hisq_links(L, seed=65)
+    det = np.linalg.det(U)
+    sig = np.sign((det / 0.9 ** 3).real)
+    assert np.array_equal(sig, O.link_sign(L, 1))
