@@ -1,0 +1,224 @@
+/*
+ * hisq.h - C ABI of the GB300 multi-right-hand-side HISQ Dslash and CG library.
+ *
+ * The operator is the HISQ staggered Dslash of Kaczmarek, Schmidt,
+ * Steinbrecher and Wagner, "Conjugate gradient solvers on Intel Xeon Phi and
+ * NVIDIA GPUs" (GPUHEP2014), Eq. 3, applied to a bundle of n right-hand
+ * sides at once as in Eq. 4:
+ *
+ *   w(x) = sum_{mu=0..3} [ U_mu(x) v(x+mu) - U_mu(x-mu)^dag v(x-mu)
+ *                         + N_mu(x) v(x+3mu) - N_mu(x-3mu)^dag v(x-3mu) ]
+ *
+ * and the conjugate-gradient inversion of the fermion matrix M = 2m + D that
+ * takes most of the runtime of the stochastic trace estimates of Eq. 2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice L[4] = {Lx, Ly, Lz, Lt}; every extent even and >= 4.
+ * Directions mu = 0,1,2,3 are x,y,z,t. V = Lx*Ly*Lz*Lt, V_h = V/2.
+ * Lexicographic site index i = x + Lx*(y + Ly*(z + Lz*t)).
+ * Parity p = (x+y+z+t) % 2. Half-lattice index h = i/2 enumerates the V_h
+ * sites of one parity in lexicographic order.
+ *
+ * Canonical links: complex128 [4][V][3][3] (mu-major, lexicographic site,
+ * row-major colour, interleaved re/im). U[mu][i] is the link from site i to
+ * i+mu, N[mu][i] the link from i to i+3mu. Staggered phases, boundary signs
+ * and the Naik coefficient are folded into the links by the caller.
+ *
+ * Spinors (colour vectors) of one parity: [V_h][3] complex, interleaved re/im,
+ * element type by hisq_prec (F64: double, F32: float, F16: IEEE half).
+ * Full-lattice vectors (only for mu != 0 solves) are parity-blocked:
+ * [2][V_h][3], the V_h even sites first.
+ *
+ * Ownership: the library owns every hisq_gauge and the workspaces cached on
+ * it (device memory it allocates with cudaMalloc and frees in
+ * hisq_gauge_free). The caller owns every spinor buffer; pointers are
+ * borrowed for the duration of the call, stream-ordered on `stream`
+ * (a cudaStream_t; NULL = legacy default stream).
+ *
+ * Errors: every call returns a hisq_status; nothing aborts or throws across
+ * the ABI. hisq_last_error() returns a thread-local message for the last
+ * failing call on this thread.
+ *
+ * Thread safety: calls on different handles are independent. Calls that
+ * share a handle must be serialised by the caller (they share workspaces).
+ */
+#ifndef HISQ_H
+#define HISQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int hisq_status;
+enum {
+    HISQ_OK = 0,
+    HISQ_EINVAL = 1,      /* bad argument: extents, n, pointer, alignment, mode */
+    HISQ_ERECON = 2,      /* links not representable in the requested compression */
+    HISQ_ENOCONV = 3,     /* CG hit maxiter before every rhs converged */
+    HISQ_EBREAKDOWN = 4,  /* CG breakdown: <p,Ap> <= 0 or not finite */
+    HISQ_ENAN = 5,        /* non-finite value in a source or residual */
+    HISQ_ECUDA = 6,       /* a CUDA runtime call failed; see hisq_last_error() */
+    HISQ_ETIMEOUT = 7,    /* reserved for bounded device-side waits */
+    HISQ_ENOMEM = 8       /* device allocation failed */
+};
+
+typedef int hisq_prec;
+enum { HISQ_F64 = 0, HISQ_F32 = 1, HISQ_F16 = 2 };
+
+typedef int hisq_recon;
+enum { HISQ_R18 = 18, HISQ_R12 = 12, HISQ_R14 = 14 };
+
+typedef struct hisq_gauge_s* hisq_gauge;
+
+/* Library version, major*10000 + minor*100 + patch. */
+int hisq_version(void);
+
+/* Message describing the last failing call on this thread ("" if none). */
+const char* hisq_last_error(void);
+
+/*
+ * Link compression, Sec. 1: the paper stores symmetric links in fewer reals
+ * and notes that for the HISQ action only the Naik links keep enough
+ * structure for it (9 or 13/14 reals). Encodings built here:
+ *   R18: all 9 complex entries.
+ *   R14: rows 1 and 2 plus one complex z; row 3 = z * conj(row1 x row2).
+ *        Exact for any link c*W, c real, W unitary (z = det(W)/c). Valid for
+ *        fat and Naik links.
+ *   R12: rows 1 and 2; row 3 = (sigma/s) * conj(row1 x row2) with sigma the
+ *        staggered sign eta_mu(x) * bc(x,mu) recomputed from coordinates
+ *        (antiperiodic t) and s = |row 1| of U[0][0]. Exact only for links
+ *        s * sigma * SU(3); fat links only (recon_N may not be R12).
+ *
+ * hisq_gauge_load packs U and N into the internal site-major SoA layout
+ * [parity][mu][complex component][V_h] in precision `prec`, and always also
+ * keeps an FP64 R18 copy used by FP64 Dslash calls and by the CG's FP64
+ * reliable updates. prec == HISQ_F64 requires R18 for both fields.
+ *   L          lattice extents (host array of 4 ints).
+ *   U, N       canonical complex128 links, device pointers if on_device != 0,
+ *              else host pointers. Read only; not retained.
+ *   recon_tol  largest allowed |reconstructed - input| entry (FP64, before
+ *              rounding to `prec`); exceeding it returns HISQ_ERECON and
+ *              no handle.
+ *   out        receives the new handle on HISQ_OK.
+ * Synchronises `stream` before returning.
+ */
+hisq_status hisq_gauge_load(const int L[4], const void* U, const void* N,
+                            int on_device, hisq_prec prec, hisq_recon recon_U,
+                            hisq_recon recon_N, double recon_tol, void* stream,
+                            hisq_gauge* out);
+
+/* Frees the handle, its link copies and every cached workspace. NULL is a no-op. */
+hisq_status hisq_gauge_free(hisq_gauge g);
+
+/* Storage precision and reconstruct modes of a handle (any pointer may be NULL). */
+hisq_status hisq_gauge_info(hisq_gauge g, int L[4], hisq_prec* prec,
+                            hisq_recon* recon_U, hisq_recon* recon_N,
+                            size_t* device_bytes);
+
+/*
+ * Tuning: Dslash right-hand sides per thread for this handle (0 = automatic,
+ * else 1, 2, 4 or 8; values that do not divide n fall back to automatic).
+ */
+hisq_status hisq_set_dslash_rpt(hisq_gauge g, int rpt);
+
+/*
+ * Compress a canonical link field to `r` reals per link (R18/R14/R12, same
+ * encodings as above) and back. Both take device pointers.
+ *   links   complex128 [4][V][3][3]
+ *   packed  double [4][V][r]
+ * hisq_link_compress also writes the largest reconstruction error to
+ * *max_err (host pointer, may be NULL). Synchronises `stream`.
+ */
+hisq_status hisq_link_compress(const int L[4], const void* links, hisq_recon r,
+                               void* packed, double* max_err, void* stream);
+hisq_status hisq_link_reconstruct(const int L[4], const void* packed,
+                                  hisq_recon r, void* links, void* stream);
+
+/*
+ * Multi-rhs Dslash, Eq. 3 and Eq. 4: w[k] = D_{p,1-p} v[k] for k < n, i.e. the
+ * output sites have parity `parity` and the inputs the opposite parity (every
+ * one- and three-hop flips parity). One launch reads every link once for all
+ * n right-hand sides.
+ *   v, w         host arrays of n device pointers, each [V_h][3] complex of
+ *                `spinor_prec`; w[k] must not alias any v[j].
+ *   n            1..16.
+ *   spinor_prec  F64 uses the FP64 R18 links; F32 and F16 use the handle's
+ *                storage copy, which must then have that same precision.
+ * hisq_dslash_ex adds a chemical potential mu on the temporal hops: forward
+ * one-hop x e^{+mu}, backward one-hop x e^{-mu}, forward Naik x e^{+3mu},
+ * backward Naik x e^{-3mu}. Asynchronous on `stream`.
+ */
+hisq_status hisq_dslash(hisq_gauge g, const void* const v[], void* const w[],
+                        int n, int parity, hisq_prec spinor_prec, void* stream);
+hisq_status hisq_dslash_ex(hisq_gauge g, double mu, const void* const v[],
+                           void* const w[], int n, int parity,
+                           hisq_prec spinor_prec, void* stream);
+
+/*
+ * Even-odd normal operator of M = 2m + D at mu = 0:
+ *   w[k] = A_e v[k] = 4 m^2 v[k] - D_eo D_oe v[k]   (even sites)
+ * A_e = (M^dag M) restricted to even sites, Hermitian positive definite.
+ * v, w as for hisq_dslash with parity 0. Uses a cached odd-parity temporary on
+ * the handle. Asynchronous on `stream`.
+ */
+hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v[],
+                       void* const w[], int n, hisq_prec spinor_prec,
+                       void* stream);
+
+/* CG parameters; hisq_cg_default_params fills the defaults noted below. */
+typedef struct {
+    int maxiter;           /* iteration cap (100000) */
+    int reliable_every;    /* FP64 reliable update every K iterations (50) */
+    double reliable_delta; /* ... or when ||r|| drops by this factor (0.1) */
+    hisq_prec inner_prec;  /* storage precision of the inner iteration (F32) */
+    int use_x0;            /* 1: x holds an initial guess on entry (0) */
+    int even_odd;          /* 1: even-odd system at mu = 0 (1) */
+    int check_every;       /* host convergence poll interval (10) */
+    int use_graphs;        /* 1: replay iterations from a captured CUDA graph (1) */
+    int rhs_per_thread;    /* Dslash rhs per thread: 0 = auto, else 1/2/4/8 */
+} hisq_cg_params;
+
+typedef struct {
+    int iters[16];             /* iterations until each rhs converged */
+    int total_iters;           /* iterations of the bundle */
+    int reliable_updates;      /* FP64 residual recomputations */
+    double true_rel_res[16];   /* final ||b - A x|| / ||b|| in FP64 per rhs */
+    double seconds;            /* wall time of the solve, host clock */
+} hisq_cg_stats;
+
+void hisq_cg_default_params(hisq_cg_params* p);
+
+/*
+ * Conjugate gradient on the normal equations of M = 2m + D, n independent
+ * CGs (one per rhs, own alpha and beta) sharing every Dslash. Stops rhs k
+ * when ||b_k - A x_k|| / ||b_k|| <= tol in FP64 (tol > 0). p may be NULL
+ * (defaults); stats may be NULL.
+ *   even_odd = 1 (requires mu == 0): (4m^2 - D_eo D_oe) x_e = b_e, b and x
+ *       [V_h][3] complex128 on even sites.
+ *   even_odd = 0: M(mu)^dag M(mu) x = b on the full lattice, with
+ *       M(mu)^dag = 2m - D(-mu); b and x parity-blocked [2][V_h][3].
+ * b[k], x[k] are device or host pointers (detected per pointer); host data
+ * is copied in and out on `stream`. The inner iteration stores vectors in
+ * p->inner_prec with FP32 arithmetic (FP64 if inner_prec is F64); every
+ * reliable update recomputes r = b - A x in FP64 with FP64 links and adds
+ * the low-precision solution increment into the FP64 x. Convergence is
+ * declared per rhs on the FP64 true residual only.
+ * Returns HISQ_OK when every rhs reached p->tol, HISQ_ENOCONV at maxiter
+ * (x holds the last iterate, stats filled), HISQ_EBREAKDOWN, HISQ_ENAN,
+ * HISQ_EINVAL (bad n, tol, pointers or mu != 0 with even_odd).
+ * Synchronises `stream` before returning.
+ */
+hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu,
+                          const void* const b[], void* const x[], int n,
+                          double tol, const hisq_cg_params* p,
+                          hisq_cg_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HISQ_H */

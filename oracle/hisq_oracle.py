@@ -33,8 +33,8 @@ Readings of the paper taken here (the paper is silent or garbled on them):
 * The chemical potential mu_chem multiplies the temporal hops: forward
   U-hop e^{+mu}, backward U^dag-hop e^{-mu}, forward Naik hop e^{+3mu},
   backward Naik hop e^{-3mu} (Eq. 1-2 need derivatives in mu).
-* "Inverting multiple vectors at the same time" (abstract, Sec. 2) is read as
-  n independent CGs sharing each Dslash, not block CG.
+* Solving for several vectors together (abstract, Sec. 2) is read as n
+  independent CGs sharing each Dslash, not block CG.
 
 Functions without a pin independent of this module are flagged in their
 docstrings; every function below is pinned by tests in ``tests/``.
@@ -128,6 +128,34 @@ def dslash(U: np.ndarray, N: np.ndarray, v: np.ndarray, mu_chem: float = 0.0) ->
         # backward Naik: N_mu(x-3mu)^dag v(x-3mu)
         w -= (1.0 / f3) * _matvec(_dagger(shift(N[mu], mu, -3, 0)), shift(v, mu, -3, 1))
     return w
+
+
+def dslash_at_sites(U: np.ndarray, N: np.ndarray, v: np.ndarray, sites, mu_chem: float = 0.0):
+    """Eq. 3 evaluated at single sites, one site at a time, for n vectors.
+
+    ``sites`` is a list of (x, y, z, t); ``v`` is (n, Lt, Lz, Ly, Lx, 3).
+    Returns (n, len(sites), 3). Used to check outputs of lattices too large
+    for the array form at a sample of sites.
+    """
+    Lt, Lz, Ly, Lx = v.shape[1:5]
+    ext = (Lx, Ly, Lz, Lt)
+    out = np.zeros((v.shape[0], len(sites), 3), dtype=COMPLEX)
+    for s, site in enumerate(sites):
+        for mu in range(4):
+            f1 = np.exp(mu_chem) if mu == 3 else 1.0
+            f3 = np.exp(3.0 * mu_chem) if mu == 3 else 1.0
+
+            def at(hops):
+                c = list(site)
+                c[mu] = (c[mu] + hops) % ext[mu]
+                return (c[3], c[2], c[1], c[0])
+
+            here = at(0)
+            out[:, s] += f1 * (v[(slice(None),) + at(+1)] @ U[mu][here].T)
+            out[:, s] -= (1.0 / f1) * (v[(slice(None),) + at(-1)] @ np.conj(U[mu][at(-1)]))
+            out[:, s] += f3 * (v[(slice(None),) + at(+3)] @ N[mu][here].T)
+            out[:, s] -= (1.0 / f3) * (v[(slice(None),) + at(-3)] @ np.conj(N[mu][at(-3)]))
+    return out
 
 
 def dslash_parity(U, N, v_half: np.ndarray, L, parity: int, mu_chem: float = 0.0) -> np.ndarray:
@@ -235,8 +263,8 @@ def dense_matrix(apply_op, shape_one) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
-# Link compression (18 -> 12 or 14 reals), Sec. 1 ("reconstruct the gauge links
-# from 8 or 12 floats ... Naik links from 9 or 13/14 floats")
+# Link compression (18 -> 12 or 14 reals), Sec. 1: fewer stored reals per
+# link, possible for the HISQ Naik links (9 or 13/14 reals in the paper)
 # ----------------------------------------------------------------------------
 #
 # The paper names the float counts but not the encodings. Readings used here:

@@ -1,0 +1,15 @@
+"""GB300-native multi-right-hand-side HISQ Dslash and conjugate gradient.
+
+The compute path is the CUDA library lib/libhisq.so (C ABI in include/hisq.h);
+``paper_1411_4439_gb300.hisq`` is its Python binding with the same names.
+Build the library with ``paper_1411_4439_gb300.build_lib.build()``.
+"""
+from . import hisq  # noqa: F401
+from .hisq import (  # noqa: F401
+    HISQ_F16, HISQ_F32, HISQ_F64, HISQ_R12, HISQ_R14, HISQ_R18, Gauge, HisqError,
+    cg_params, hisq_cg_default_params, hisq_cg_solve, hisq_dslash, hisq_dslash_ex,
+    hisq_gauge_free, hisq_gauge_info, hisq_gauge_load, hisq_link_compress,
+    hisq_link_reconstruct, hisq_mdagm, hisq_set_dslash_rpt, hisq_version,
+)
+
+__all__ = [n for n in dir() if n.startswith(("hisq_", "HISQ_"))] + ["Gauge", "HisqError", "cg_params"]

@@ -1,0 +1,364 @@
+// Multi-rhs HISQ Dslash kernel, Eq. 3 applied to a bundle of rhs as in Eq. 4.
+//
+// One thread owns one output site and RPT right-hand sides; blockDim.y groups
+// split the bundle (nrhs = blockDim.y * RPT), so all groups of a block share
+// the same sites and re-read the same links from L1. Per output site the 16
+// hops (4 directions x {+1, -1, +3, -3}) each load one link once for all RPT
+// rhs and gather RPT neighbour vectors. Links are reconstructed in registers
+// (R12 / R14), temporal links are rescaled by the chemical-potential factors,
+// and the epilogue forms out = [y] + cx * x + cd * (D in) and, optionally, the
+// per-rhs reductions the CG needs (Re<x,out> or |out|^2 and max|out_i|).
+#pragma once
+
+#include "hisq_internal.cuh"
+#include "reduce.cuh"
+
+namespace hisq {
+
+template <typename RC>
+struct Link {
+    RC e[9];
+};
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+// acc += a * b
+template <typename RC>
+__device__ __forceinline__ void cmadd(RC& acc, const RC a, const RC b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+
+// acc -= conj(a) * b
+template <typename RC>
+__device__ __forceinline__ void cmsub_conj(RC& acc, const RC a, const RC b) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+
+template <typename RC>
+__device__ __forceinline__ RC cmul(const RC a, const RC b) {
+    RC c;
+    c.x = a.x * b.x - a.y * b.y;
+    c.y = a.x * b.y + a.y * b.x;
+    return c;
+}
+
+// row3 = f * conj(row1 x row2), f complex
+template <typename RC>
+__device__ __forceinline__ void third_row(Link<RC>& m, const RC f) {
+    RC c0, c1, c2;
+    c0 = cmul(m.e[1], m.e[5]);
+    c0.x -= m.e[2].x * m.e[4].x - m.e[2].y * m.e[4].y;
+    c0.y -= m.e[2].x * m.e[4].y + m.e[2].y * m.e[4].x;
+    c1 = cmul(m.e[2], m.e[3]);
+    c1.x -= m.e[0].x * m.e[5].x - m.e[0].y * m.e[5].y;
+    c1.y -= m.e[0].x * m.e[5].y + m.e[0].y * m.e[5].x;
+    c2 = cmul(m.e[0], m.e[4]);
+    c2.x -= m.e[1].x * m.e[3].x - m.e[1].y * m.e[3].y;
+    c2.y -= m.e[1].x * m.e[3].y + m.e[1].y * m.e[3].x;
+    c0.y = -c0.y;
+    c1.y = -c1.y;
+    c2.y = -c2.y;
+    m.e[6] = cmul(f, c0);
+    m.e[7] = cmul(f, c1);
+    m.e[8] = cmul(f, c2);
+}
+
+// Load one link of `recon` reals stored at [comp][vh] from `base` (already
+// offset to the (parity, mu) slab), site index `idx`. `sign` is the staggered
+// sign used by R12 (ignored otherwise).
+template <typename LC, int RECON, typename RC>
+__device__ __forceinline__ void load_link(Link<RC>& m, const LC* __restrict__ base, int vh,
+                                          int idx, typename Traits<float>::R inv_s_f,
+                                          double inv_s_d, int sign) {
+    using R = decltype(RC{}.x);
+    constexpr int NC = (RECON == 18) ? 9 : (RECON == 14 ? 7 : 6);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const auto v = ld_c(base + (size_t)c * vh + idx);
+        m.e[c].x = (R)v.x;
+        m.e[c].y = (R)v.y;
+    }
+    if (RECON == 18) {
+#pragma unroll
+        for (int c = 6; c < 9; ++c) {
+            const auto v = ld_c(base + (size_t)c * vh + idx);
+            m.e[c].x = (R)v.x;
+            m.e[c].y = (R)v.y;
+        }
+    } else if (RECON == 14) {
+        const auto zv = ld_c(base + (size_t)(NC - 1) * vh + idx);
+        RC z;
+        z.x = (R)zv.x;
+        z.y = (R)zv.y;
+        third_row(m, z);
+    } else {
+        RC f;
+        const R inv_s = (sizeof(R) == 8) ? (R)inv_s_d : (R)inv_s_f;
+        f.x = sign > 0 ? inv_s : -inv_s;
+        f.y = (R)0;
+        third_row(m, f);
+    }
+}
+
+template <typename RC, typename R>
+__device__ __forceinline__ void scale_link(Link<RC>& m, const R f) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        m.e[c].x *= f;
+        m.e[c].y *= f;
+    }
+}
+
+template <typename SC, typename RC>
+__device__ __forceinline__ void load_spinor(RC (&v)[3], const void* p, int idx) {
+    using R = decltype(RC{}.x);
+    const SC* s = reinterpret_cast<const SC*>(p) + 3 * (size_t)idx;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const auto t = ld_c(s + c);
+        v[c].x = (R)t.x;
+        v[c].y = (R)t.y;
+    }
+}
+
+// acc[i] += sum_j m_ij v_j
+template <typename RC>
+__device__ __forceinline__ void mv_add(RC (&acc)[3], const Link<RC>& m, const RC (&v)[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cmadd(acc[i], m.e[3 * i + j], v[j]);
+}
+
+// acc[i] -= sum_j conj(m_ji) v_j
+template <typename RC>
+__device__ __forceinline__ void mv_sub_dag(RC (&acc)[3], const Link<RC>& m, const RC (&v)[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cmsub_conj(acc[i], m.e[3 * j + i], v[j]);
+}
+
+__device__ __forceinline__ int wrap(int c, int L) {
+    c = (c >= L) ? c - L : c;
+    return (c < 0) ? c + L : c;
+}
+
+template <typename S, typename LS, int RU, int RN, int RPT, int EPI>
+__global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs a) {
+    using R = typename Traits<S>::R;
+    using RC = typename Cx<R>::T;
+    using SC = typename Traits<S>::C;
+    using LC = typename Traits<LS>::C;
+    constexpr int NCU = (RU == 18) ? 9 : (RU == 14 ? 7 : 6);
+    constexpr int NCN = (RN == 18) ? 9 : (RN == 14 ? 7 : 6);
+
+    const Geom& g = a.g;
+    const int vh = g.vh;
+    const int p = a.parity, q = 1 - p;
+    const int k0 = threadIdx.y * RPT;
+    const LC* __restrict__ Ub = reinterpret_cast<const LC*>(a.U);
+    const LC* __restrict__ Nb = reinterpret_cast<const LC*>(a.N);
+    const float inv_s_f = (float)a.r12_inv_scale;
+
+    R red0[RPT], red1[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        red0[j] = (R)0;
+        red1[j] = (R)0;
+    }
+
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < vh; h += gridDim.x * blockDim.x) {
+        // coordinates of output site h of parity p
+        const int xh = h % g.hx;
+        int r = h / g.hx;
+        const int y = r % g.L[1];
+        r /= g.L[1];
+        const int z = r % g.L[2];
+        const int t = r / g.L[2];
+        const int x = 2 * xh + ((p + y + z + t) & 1);
+        const int hrow = h - xh;
+
+        RC acc[RPT][3];
+#pragma unroll
+        for (int j = 0; j < RPT; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[j][c].x = (R)0;
+                acc[j][c].y = (R)0;
+            }
+
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const int coord = (mu == 0) ? x : (mu == 1) ? y : (mu == 2) ? z : t;
+            const int ext = g.L[mu];
+            const int stride = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
+            // staggered sign of this site's mu links (R12 only); eta_mu(x - mu) = eta_mu(x)
+            int eta = 1;
+            if (RU == 12) {
+                const int e = (mu == 0) ? 0 : (mu == 1) ? x : (mu == 2) ? (x + y) : (x + y + z);
+                eta = (e & 1) ? -1 : 1;
+            }
+            const LC* Uf = Ub + (size_t)(p * 4 + mu) * NCU * vh;
+            const LC* Ubk = Ub + (size_t)(q * 4 + mu) * NCU * vh;
+            const LC* Nf = Nb + (size_t)(p * 4 + mu) * NCN * vh;
+            const LC* Nbk = Nb + (size_t)(q * 4 + mu) * NCN * vh;
+
+#pragma unroll
+            for (int hop = 0; hop < 4; ++hop) {
+                const int d = (hop == 0) ? 1 : (hop == 1) ? -1 : (hop == 2) ? 3 : -3;
+                const int cn = wrap(coord + d, ext);
+                const int hn = (mu == 0) ? hrow + (cn >> 1) : h + (cn - coord) * stride;
+                Link<RC> m;
+                if (hop == 0) {
+                    const int sgn = (RU == 12 && mu == 3 && t == ext - 1) ? -eta : eta;
+                    load_link<LC, RU, RC>(m, Uf, vh, h, inv_s_f, a.r12_inv_scale, sgn);
+                } else if (hop == 1) {
+                    const int sgn = (RU == 12 && mu == 3 && t == 0) ? -eta : eta;
+                    load_link<LC, RU, RC>(m, Ubk, vh, hn, inv_s_f, a.r12_inv_scale, sgn);
+                } else if (hop == 2) {
+                    load_link<LC, RN, RC>(m, Nf, vh, h, inv_s_f, a.r12_inv_scale, 1);
+                } else {
+                    load_link<LC, RN, RC>(m, Nbk, vh, hn, inv_s_f, a.r12_inv_scale, 1);
+                }
+                if (mu == 3 && a.has_mu) {
+                    const double f = (hop == 0) ? a.ft1 : (hop == 1) ? a.bt1 : (hop == 2) ? a.ft3 : a.bt3;
+                    scale_link(m, (R)f);
+                }
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    RC v[3];
+                    load_spinor<SC, RC>(v, a.in[k0 + j], hn);
+                    if (hop == 0 || hop == 2)
+                        mv_add(acc[j], m, v);
+                    else
+                        mv_sub_dag(acc[j], m, v);
+                }
+            }
+        }
+
+        // epilogue
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int k = k0 + j;
+            RC w[3];
+            if (EPI == EPI_NONE) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) w[c] = acc[j][c];
+            } else {
+                RC xv[3];
+                load_spinor<SC, RC>(xv, a.x[k], h);
+                const R cx = (R)a.cx, cd = (R)a.cd;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    w[c].x = fma(cd, acc[j][c].x, cx * xv[c].x);
+                    w[c].y = fma(cd, acc[j][c].y, cx * xv[c].y);
+                }
+                if (EPI == EPI_XY) {
+                    RC yv[3];
+                    load_spinor<SC, RC>(yv, a.y[k], h);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        w[c].x += yv[c].x;
+                        w[c].y += yv[c].y;
+                    }
+                }
+                if (a.red_mode == RED_DOT_XW) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        red0[j] = fma(xv[c].x, w[c].x, red0[j]);
+                        red0[j] = fma(xv[c].y, w[c].y, red0[j]);
+                    }
+                }
+            }
+            SC* o = reinterpret_cast<SC*>(a.out[k]) + 3 * (size_t)h;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) st_c(o + c, w[c]);
+            if (a.red_mode == RED_NORM_MAX_W) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    // reduce what was stored, so the norm matches the stored vector
+                    const RC sv = stored_value(w[c], o);
+                    const R n2 = sv.x * sv.x + sv.y * sv.y;
+                    red0[j] += n2;
+                    red1[j] = fmax(red1[j], sqrt(n2));
+                }
+            }
+        }
+    }
+
+    if (a.red_mode == RED_NONE) return;
+
+    // per-rhs block reduction: warp (fixed tree) -> shared -> partial slot
+    __shared__ double s_part[kMaxRedVals][8];
+    __shared__ double s_vals[kMaxRedVals];
+    const int nv = (a.red_mode == RED_NORM_MAX_W) ? 2 : 1;
+    const int lane = threadIdx.x & 31;
+    const int wig = threadIdx.x >> 5;            // warp index within the group
+    const int wpg = blockDim.x >> 5;             // warps per group
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const double s0 = (double)warp_sum(red0[j]);
+        const double s1 = (double)warp_max(red1[j]);
+        if (lane == 0) {
+            s_part[(k0 + j) * nv][wig] = s0;
+            if (nv == 2) s_part[(k0 + j) * nv + 1][wig] = s1;
+        }
+    }
+    __syncthreads();
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nvals = a.nrhs * nv;
+    if (tid < nvals) {
+        const bool is_max = (nv == 2) && (tid & 1);
+        double acc = 0.0;
+        for (int w = 0; w < wpg; ++w) acc = is_max ? fmax(acc, s_part[tid][w]) : acc + s_part[tid][w];
+        a.red.partials[(size_t)tid * kMaxRedBlocks + blockIdx.x] = acc;
+    }
+    if (!last_block_arrive(a.red.counter, gridDim.x)) return;
+    finish_values(a.red, nvals, gridDim.x, [nv](int v) { return nv == 2 && (v & 1); }, s_vals);
+    if (a.finish == FIN_CG_ALPHA) {
+        finish_cg_alpha(a.cg, s_vals, a.nrhs);
+    } else if (a.finish == FIN_RELIABLE) {
+        finish_reliable(a.cg, s_vals, a.nrhs, a.tol2);
+    } else if (a.red_out != nullptr && tid < nvals) {
+        a.red_out[tid] = s_vals[tid];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launcher for one instance
+// ---------------------------------------------------------------------------
+template <typename S, typename LS, int RU, int RN, int RPT, int EPI>
+cudaError_t launch_dslash_instance(const DslashArgs& a, cudaStream_t s) {
+    const int G = a.nrhs / RPT;
+    if (G < 1 || G * RPT != a.nrhs || G > kMaxRhs) return cudaErrorInvalidValue;
+    int bx = 256 / G;
+    if (bx < 32) bx = 32;
+    bx &= ~31;
+    const dim3 block(bx, G);
+    static int occ_cache[kMaxRhs + 1] = {0};
+    int occ = occ_cache[G];
+    if (occ == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, dslash_kernel<S, LS, RU, RN, RPT, EPI>, bx * G, 0);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+        occ_cache[G] = occ;
+    }
+    long long nblk = ((long long)a.g.vh + bx - 1) / bx;
+    long long cap = (long long)occ * device_sm_count();
+    if (nblk > cap) nblk = cap;
+    if (nblk > kMaxRedBlocks) nblk = kMaxRedBlocks;
+    dslash_kernel<S, LS, RU, RN, RPT, EPI><<<(unsigned)nblk, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace hisq

@@ -1,0 +1,924 @@
+// C ABI of libhisq: gauge handles, Dslash and normal-operator entry points,
+// and the mixed-precision multi-rhs CG driver.
+//
+// The CG (Hestenes-Stiefel, one independent CG per rhs sharing each Dslash)
+// keeps all of its scalars on the device: alpha and beta are formed by the
+// last block of the reduction that produces their numerators/denominators,
+// so an iteration is four kernel launches with no host round trip. The host
+// polls the scalars every `check_every` iterations to decide on FP64
+// reliable updates (every `reliable_every` iterations, or when a residual
+// fell by `reliable_delta`, or when an iterated residual claims
+// convergence), and replays the iterations from a captured CUDA graph.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hisq_internal.cuh"
+
+using namespace hisq;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hisq_status fail(hisq_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define HISQ_CUDA(call)                                                                   \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? HISQ_ENOMEM : HISQ_ECUDA,       \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                        \
+    } while (0)
+
+size_t prec_complex_bytes(int prec) {
+    return prec == HISQ_F64 ? 16 : prec == HISQ_F32 ? 8 : 4;
+}
+
+bool valid_prec(int p) { return p == HISQ_F64 || p == HISQ_F32 || p == HISQ_F16; }
+
+hisq_status make_geom(const int L[4], Geom* g) {
+    if (L == nullptr) return fail(HISQ_EINVAL, "lattice extents pointer is NULL");
+    long long V = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (L[m] < 4 || (L[m] & 1))
+            return fail(HISQ_EINVAL, "extent L[%d] = %d must be even and >= 4", m, L[m]);
+        V *= L[m];
+    }
+    // internal link slabs index up to 2 * 4 * 9 * V_h elements with 32-bit site math
+    if (V / 2 > (1ll << 26)) return fail(HISQ_EINVAL, "lattice too large (V = %lld)", V);
+    for (int m = 0; m < 4; ++m) g->L[m] = L[m];
+    g->hx = L[0] / 2;
+    g->vh = (int)(V / 2);
+    g->sy = g->hx;
+    g->sz = g->hx * L[1];
+    g->st = g->hx * L[1] * L[2];
+    return HISQ_OK;
+}
+
+// Device pointer test: memory the GPU can address directly (device or managed).
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+namespace hisq {
+int device_sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+}  // namespace hisq
+
+// ---------------------------------------------------------------------------
+// Workspaces
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GraphKey {
+    int chunk;
+    double mass, mu;
+    int rpt;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(chunk, mass, mu, rpt) < std::tie(o.chunk, o.mass, o.mu, o.rpt);
+    }
+};
+
+struct Workspace {
+    int n = 0, prec = 0, full = 0;
+    long long len = 0;           // complex numbers per rhs of one CG vector
+    long long len_half = 0;      // complex numbers per rhs of one parity (3 V_h)
+    void* r_lo = nullptr;
+    void* p_lo = nullptr;
+    void* Ap_lo = nullptr;
+    void* x_lo = nullptr;
+    void* t_lo = nullptr;        // operator temporary
+    double2* b_hi = nullptr;
+    double2* x_hi = nullptr;
+    double2* r_hi = nullptr;
+    double2* t_hi = nullptr;
+    CgScalars* cg = nullptr;
+    CgScalars* cg_host = nullptr;
+    double* partials = nullptr;
+    unsigned int* counter = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    size_t bytes = 0;
+};
+
+void free_workspace(Workspace* w) {
+    if (!w) return;
+    for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
+    void* ptrs[] = {w->r_lo, w->p_lo, w->Ap_lo, w->x_lo, w->t_lo, w->b_hi, w->x_hi,
+                    w->r_hi, w->t_hi, w->cg, w->partials, w->counter};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (w->cg_host) cudaFreeHost(w->cg_host);
+    if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
+    delete w;
+}
+
+}  // namespace
+
+struct hisq_gauge_s {
+    Geom g;
+    int device = 0;
+    int prec = HISQ_F32, recon_U = 18, recon_N = 18;
+    double r12_inv_scale = 1.0;
+    void* U_lo = nullptr;        // storage copy (prec, recon)
+    void* N_lo = nullptr;
+    double2* U64 = nullptr;      // FP64 R18 copy
+    double2* N64 = nullptr;
+    size_t link_bytes = 0;
+    int rpt_override = 0;
+    void* mdagm_tmp = nullptr;
+    size_t mdagm_tmp_bytes = 0;
+    std::vector<Workspace*> ws;
+    std::mutex mtx;
+};
+
+extern "C" int hisq_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+extern "C" const char* hisq_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Gauge handles
+// ---------------------------------------------------------------------------
+namespace {
+
+hisq_status pack_field(hisq_gauge g, const double2* canon, int prec, int recon, int hop,
+                       double recon_tol, void** out, size_t* bytes, const char* name,
+                       cudaStream_t s) {
+    const size_t nc = (size_t)recon / 2;
+    const size_t sz = 2 * 4 * nc * (size_t)g->g.vh * prec_complex_bytes(prec);
+    HISQ_CUDA(cudaMalloc(out, sz));
+    *bytes += sz;
+    unsigned long long* err_bits = nullptr;
+    HISQ_CUDA(cudaMalloc(&err_bits, sizeof(unsigned long long)));
+    HISQ_CUDA(cudaMemsetAsync(err_bits, 0, sizeof(unsigned long long), s));
+    cudaError_t e = launch_pack_links(g->g, canon, prec, recon, hop, g->r12_inv_scale, *out,
+                                      err_bits, s);
+    unsigned long long bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, err_bits, sizeof(bits), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(err_bits);
+    HISQ_CUDA(e);
+    double err;
+    memcpy(&err, &bits, sizeof(err));
+    if (!(err <= recon_tol))
+        return fail(HISQ_ERECON, "%s links are not representable with %d reals: max reconstruct error %.3e > tol %.3e",
+                    name, recon, err, recon_tol);
+    return HISQ_OK;
+}
+
+void destroy_gauge(hisq_gauge g) {
+    if (!g) return;
+    for (Workspace* w : g->ws) free_workspace(w);
+    if (g->U_lo && g->U_lo != g->U64) cudaFree(g->U_lo);
+    if (g->N_lo && g->N_lo != g->N64) cudaFree(g->N_lo);
+    if (g->U64) cudaFree(g->U64);
+    if (g->N64) cudaFree(g->N64);
+    if (g->mdagm_tmp) cudaFree(g->mdagm_tmp);
+    delete g;
+}
+
+}  // namespace
+
+extern "C" hisq_status hisq_gauge_load(const int L[4], const void* U, const void* N, int on_device,
+                                       hisq_prec prec, hisq_recon recon_U, hisq_recon recon_N,
+                                       double recon_tol, void* stream, hisq_gauge* out) {
+    if (out == nullptr) return fail(HISQ_EINVAL, "out handle pointer is NULL");
+    *out = nullptr;
+    if (U == nullptr || N == nullptr) return fail(HISQ_EINVAL, "link pointer is NULL");
+    if (!valid_prec(prec)) return fail(HISQ_EINVAL, "unknown precision %d", prec);
+    if (recon_U != 18 && recon_U != 12 && recon_U != 14)
+        return fail(HISQ_EINVAL, "recon_U must be 18, 12 or 14 (got %d)", recon_U);
+    if (recon_N != 18 && recon_N != 14)
+        return fail(HISQ_EINVAL, "recon_N must be 18 or 14 (got %d)", recon_N);
+    if (prec == HISQ_F64 && (recon_U != 18 || recon_N != 18))
+        return fail(HISQ_EINVAL, "F64 storage requires R18 for both fields");
+    if (!dslash_variant_supported(prec, recon_U, recon_N, EPI_NONE))
+        return fail(HISQ_EINVAL, "no Dslash kernel for recon (%d, %d)", recon_U, recon_N);
+    if (!(recon_tol >= 0.0)) return fail(HISQ_EINVAL, "recon_tol must be >= 0");
+    Geom geom;
+    hisq_status st = make_geom(L, &geom);
+    if (st != HISQ_OK) return st;
+    if (on_device && (!is_device_pointer(U) || !is_device_pointer(N)))
+        return fail(HISQ_EINVAL, "on_device = 1 but a link pointer is not device memory");
+
+    cudaStream_t s = (cudaStream_t)stream;
+    hisq_gauge g = new hisq_gauge_s();
+    g->g = geom;
+    cudaGetDevice(&g->device);
+    g->prec = prec;
+    g->recon_U = recon_U;
+    g->recon_N = recon_N;
+    const size_t canon_bytes = (size_t)4 * 2 * geom.vh * 9 * sizeof(double2);
+    const double2* cu = (const double2*)U;
+    const double2* cn = (const double2*)N;
+    double2* stage = nullptr;
+    auto cleanup = [&](hisq_status code) {
+        if (stage) cudaFree(stage);
+        if (code != HISQ_OK) destroy_gauge(g);
+        return code;
+    };
+    if (!on_device) {
+        if (cudaMalloc(&stage, 2 * canon_bytes) != cudaSuccess)
+            return cleanup(fail(HISQ_ENOMEM, "cannot allocate %zu bytes to stage links", 2 * canon_bytes));
+        if (cudaMemcpyAsync(stage, U, canon_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(stage + canon_bytes / sizeof(double2), N, canon_bytes,
+                            cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return cleanup(fail(HISQ_ECUDA, "link upload failed: %s", cudaGetErrorString(cudaGetLastError())));
+        cu = stage;
+        cn = stage + canon_bytes / sizeof(double2);
+    }
+    if (recon_U == 12) {
+        // s = |row 1| of U_0 at site 0
+        double2 row[3];
+        if (cudaMemcpyAsync(row, cu, sizeof(row), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return cleanup(fail(HISQ_ECUDA, "reading U[0][0] failed"));
+        const double sc = std::sqrt(row[0].x * row[0].x + row[0].y * row[0].y + row[1].x * row[1].x +
+                                    row[1].y * row[1].y + row[2].x * row[2].x + row[2].y * row[2].y);
+        if (!(sc > 0.0)) return cleanup(fail(HISQ_ERECON, "R12 needs a nonzero first row in U[0][0]"));
+        g->r12_inv_scale = 1.0 / sc;
+    }
+    size_t bytes = 0;
+    st = pack_field(g, cu, HISQ_F64, 18, 1, recon_tol, (void**)&g->U64, &bytes, "fat", s);
+    if (st == HISQ_OK) st = pack_field(g, cn, HISQ_F64, 18, 3, recon_tol, (void**)&g->N64, &bytes, "Naik", s);
+    if (st == HISQ_OK) {
+        if (prec == HISQ_F64) {
+            g->U_lo = g->U64;
+            g->N_lo = g->N64;
+        } else {
+            st = pack_field(g, cu, prec, recon_U, 1, recon_tol, &g->U_lo, &bytes, "fat", s);
+            if (st == HISQ_OK) st = pack_field(g, cn, prec, recon_N, 3, recon_tol, &g->N_lo, &bytes, "Naik", s);
+        }
+    }
+    if (st != HISQ_OK) return cleanup(st);
+    g->link_bytes = bytes;
+    *out = g;
+    return cleanup(HISQ_OK);
+}
+
+extern "C" hisq_status hisq_gauge_free(hisq_gauge g) {
+    if (!g) return HISQ_OK;
+    destroy_gauge(g);
+    return HISQ_OK;
+}
+
+extern "C" hisq_status hisq_gauge_info(hisq_gauge g, int L[4], hisq_prec* prec, hisq_recon* recon_U,
+                                       hisq_recon* recon_N, size_t* device_bytes) {
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    if (L)
+        for (int m = 0; m < 4; ++m) L[m] = g->g.L[m];
+    if (prec) *prec = g->prec;
+    if (recon_U) *recon_U = g->recon_U;
+    if (recon_N) *recon_N = g->recon_N;
+    if (device_bytes) {
+        size_t b = g->link_bytes + g->mdagm_tmp_bytes;
+        for (Workspace* w : g->ws) b += w->bytes;
+        *device_bytes = b;
+    }
+    return HISQ_OK;
+}
+
+extern "C" hisq_status hisq_set_dslash_rpt(hisq_gauge g, int rpt) {
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    if (rpt != 0 && rpt != 1 && rpt != 2 && rpt != 4 && rpt != 8)
+        return fail(HISQ_EINVAL, "rhs per thread must be 0 (auto), 1, 2, 4 or 8");
+    g->rpt_override = rpt;
+    return HISQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Link compression helpers
+// ---------------------------------------------------------------------------
+extern "C" hisq_status hisq_link_compress(const int L[4], const void* links, hisq_recon r,
+                                          void* packed, double* max_err, void* stream) {
+    Geom g;
+    hisq_status st = make_geom(L, &g);
+    if (st != HISQ_OK) return st;
+    if (r != 18 && r != 14 && r != 12) return fail(HISQ_EINVAL, "recon must be 18, 14 or 12");
+    if (!links || !packed) return fail(HISQ_EINVAL, "NULL pointer");
+    if (!is_device_pointer(links) || !is_device_pointer(packed))
+        return fail(HISQ_EINVAL, "link_compress takes device pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    double inv_s = 1.0;
+    if (r == 12) {
+        double2 row[3];
+        HISQ_CUDA(cudaMemcpyAsync(row, links, sizeof(row), cudaMemcpyDeviceToHost, s));
+        HISQ_CUDA(cudaStreamSynchronize(s));
+        const double sc = std::sqrt(row[0].x * row[0].x + row[0].y * row[0].y + row[1].x * row[1].x +
+                                    row[1].y * row[1].y + row[2].x * row[2].x + row[2].y * row[2].y);
+        if (!(sc > 0.0)) return fail(HISQ_ERECON, "R12 needs a nonzero first row in link 0");
+        inv_s = 1.0 / sc;
+    }
+    unsigned long long* bits_d = nullptr;
+    HISQ_CUDA(cudaMalloc(&bits_d, sizeof(unsigned long long)));
+    cudaError_t e = cudaMemsetAsync(bits_d, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = launch_compress_links(g, (const double2*)links, r, 1, inv_s, (double*)packed, bits_d, s);
+    unsigned long long bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, bits_d, sizeof(bits), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(bits_d);
+    HISQ_CUDA(e);
+    if (max_err) memcpy(max_err, &bits, sizeof(double));
+    return HISQ_OK;
+}
+
+extern "C" hisq_status hisq_link_reconstruct(const int L[4], const void* packed, hisq_recon r,
+                                             void* links, void* stream) {
+    Geom g;
+    hisq_status st = make_geom(L, &g);
+    if (st != HISQ_OK) return st;
+    if (r != 18 && r != 14 && r != 12) return fail(HISQ_EINVAL, "recon must be 18, 14 or 12");
+    if (!links || !packed) return fail(HISQ_EINVAL, "NULL pointer");
+    if (!is_device_pointer(links) || !is_device_pointer(packed))
+        return fail(HISQ_EINVAL, "link_reconstruct takes device pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    double inv_s = 1.0;
+    if (r == 12) {
+        // row 1 of link 0 is stored verbatim: its norm is s
+        double v[6];
+        HISQ_CUDA(cudaMemcpyAsync(v, packed, sizeof(v), cudaMemcpyDeviceToHost, s));
+        HISQ_CUDA(cudaStreamSynchronize(s));
+        double n2 = 0;
+        for (double a : v) n2 += a * a;
+        if (!(n2 > 0.0)) return fail(HISQ_ERECON, "R12 needs a nonzero first row in link 0");
+        inv_s = 1.0 / std::sqrt(n2);
+    }
+    HISQ_CUDA(launch_reconstruct_links(g, (const double*)packed, r, 1, inv_s, (double2*)links, s));
+    HISQ_CUDA(cudaStreamSynchronize(s));
+    return HISQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Dslash and normal operator
+// ---------------------------------------------------------------------------
+namespace {
+
+int auto_rpt(int n, int prec) {
+    const int mx = dslash_max_rpt(prec);
+    int r = 1;
+    while (r * 2 <= mx && n % (r * 2) == 0) r *= 2;
+    while (n / r > 8 && r < mx) r *= 2;   // at most 8 rhs groups per block
+    return r;
+}
+
+int pick_rpt(hisq_gauge g, int n, int prec, int requested) {
+    int r = requested ? requested : g->rpt_override;
+    if (r == 0 || r > dslash_max_rpt(prec) || n % r != 0 || n / r > 8) r = auto_rpt(n, prec);
+    return r;
+}
+
+bool aligned_for(const void* p, int prec) {
+    return ((uintptr_t)p % prec_complex_bytes(prec)) == 0;
+}
+
+void fill_common(DslashArgs& a, hisq_gauge g, int prec, int parity, int n) {
+    memset(&a, 0, sizeof(a));
+    a.g = g->g;
+    a.parity = parity;
+    a.nrhs = n;
+    a.U = (prec == HISQ_F64) ? (const void*)g->U64 : g->U_lo;
+    a.N = (prec == HISQ_F64) ? (const void*)g->N64 : g->N_lo;
+    a.cx = 0.0;
+    a.cd = 1.0;
+    a.ft1 = a.bt1 = a.ft3 = a.bt3 = 1.0;
+    a.has_mu = 0;
+    a.r12_inv_scale = g->r12_inv_scale;
+    a.red_mode = RED_NONE;
+    a.finish = FIN_STORE;
+}
+
+void set_mu(DslashArgs& a, double mu) {
+    a.ft1 = std::exp(mu);
+    a.bt1 = std::exp(-mu);
+    a.ft3 = std::exp(3.0 * mu);
+    a.bt3 = std::exp(-3.0 * mu);
+    a.has_mu = (mu != 0.0) ? 1 : 0;
+}
+
+int link_recon_u(hisq_gauge g, int prec) { return prec == HISQ_F64 ? 18 : g->recon_U; }
+int link_recon_n(hisq_gauge g, int prec) { return prec == HISQ_F64 ? 18 : g->recon_N; }
+
+hisq_status check_spinors(hisq_gauge g, const void* const v[], void* const w[], int n, int prec) {
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
+    if (!valid_prec(prec)) return fail(HISQ_EINVAL, "unknown spinor precision %d", prec);
+    if (prec != HISQ_F64 && prec != g->prec)
+        return fail(HISQ_EINVAL, "spinor precision %d needs links stored in the same precision (handle has %d)",
+                    prec, g->prec);
+    if (!v || !w) return fail(HISQ_EINVAL, "NULL pointer array");
+    for (int k = 0; k < n; ++k) {
+        if (!v[k] || !w[k]) return fail(HISQ_EINVAL, "NULL spinor pointer for rhs %d", k);
+        if (!aligned_for(v[k], prec) || !aligned_for(w[k], prec))
+            return fail(HISQ_EINVAL, "spinor pointer for rhs %d is not %zu-byte aligned", k,
+                        prec_complex_bytes(prec));
+    }
+    return HISQ_OK;
+}
+
+}  // namespace
+
+extern "C" hisq_status hisq_dslash_ex(hisq_gauge g, double mu, const void* const v[], void* const w[],
+                                      int n, int parity, hisq_prec spinor_prec, void* stream) {
+    hisq_status st = check_spinors(g, v, w, n, spinor_prec);
+    if (st != HISQ_OK) return st;
+    if (parity != 0 && parity != 1) return fail(HISQ_EINVAL, "parity must be 0 or 1");
+    if (!std::isfinite(mu)) return fail(HISQ_EINVAL, "mu must be finite");
+    DslashArgs a;
+    fill_common(a, g, spinor_prec, parity, n);
+    set_mu(a, mu);
+    for (int k = 0; k < n; ++k) {
+        a.in[k] = v[k];
+        a.out[k] = w[k];
+    }
+    const int rpt = pick_rpt(g, n, spinor_prec, 0);
+    HISQ_CUDA(launch_dslash(a, spinor_prec, link_recon_u(g, spinor_prec), link_recon_n(g, spinor_prec),
+                            EPI_NONE, rpt, (cudaStream_t)stream));
+    return HISQ_OK;
+}
+
+extern "C" hisq_status hisq_dslash(hisq_gauge g, const void* const v[], void* const w[], int n,
+                                   int parity, hisq_prec spinor_prec, void* stream) {
+    return hisq_dslash_ex(g, 0.0, v, w, n, parity, spinor_prec, stream);
+}
+
+extern "C" hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v[], void* const w[],
+                                  int n, hisq_prec spinor_prec, void* stream) {
+    hisq_status st = check_spinors(g, v, w, n, spinor_prec);
+    if (st != HISQ_OK) return st;
+    if (!std::isfinite(mass)) return fail(HISQ_EINVAL, "mass must be finite");
+    const size_t per = (size_t)g->g.vh * 3 * prec_complex_bytes(spinor_prec);
+    std::lock_guard<std::mutex> lock(g->mtx);
+    if (g->mdagm_tmp_bytes < per * n) {
+        if (g->mdagm_tmp) cudaFree(g->mdagm_tmp);
+        g->mdagm_tmp = nullptr;
+        g->mdagm_tmp_bytes = 0;
+        HISQ_CUDA(cudaMalloc(&g->mdagm_tmp, per * kMaxRhs));
+        g->mdagm_tmp_bytes = per * kMaxRhs;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int rpt = pick_rpt(g, n, spinor_prec, 0);
+    const int ru = link_recon_u(g, spinor_prec), rn = link_recon_n(g, spinor_prec);
+    DslashArgs a;
+    fill_common(a, g, spinor_prec, 1, n);
+    for (int k = 0; k < n; ++k) {
+        a.in[k] = v[k];
+        a.out[k] = (char*)g->mdagm_tmp + per * k;
+    }
+    HISQ_CUDA(launch_dslash(a, spinor_prec, ru, rn, EPI_NONE, rpt, s));
+    DslashArgs b;
+    fill_common(b, g, spinor_prec, 0, n);
+    b.cx = 4.0 * mass * mass;
+    b.cd = -1.0;
+    for (int k = 0; k < n; ++k) {
+        b.in[k] = (char*)g->mdagm_tmp + per * k;
+        b.out[k] = w[k];
+        b.x[k] = v[k];
+    }
+    HISQ_CUDA(launch_dslash(b, spinor_prec, ru, rn, EPI_X, rpt, s));
+    return HISQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Conjugate gradient
+// ---------------------------------------------------------------------------
+extern "C" void hisq_cg_default_params(hisq_cg_params* p) {
+    if (!p) return;
+    p->maxiter = 100000;
+    p->reliable_every = 50;
+    p->reliable_delta = 0.1;
+    p->inner_prec = HISQ_F32;
+    p->use_x0 = 0;
+    p->even_odd = 1;
+    p->check_every = 10;
+    p->use_graphs = 1;
+    p->rhs_per_thread = 0;
+}
+
+namespace {
+
+hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** out) {
+    for (Workspace* w : g->ws)
+        if (w->n == n && w->prec == prec && w->full == full) {
+            *out = w;
+            return HISQ_OK;
+        }
+    Workspace* w = new Workspace();
+    w->n = n;
+    w->prec = prec;
+    w->full = full;
+    w->len_half = 3ll * g->g.vh;
+    w->len = full ? 2 * w->len_half : w->len_half;
+    const size_t lo = (size_t)n * w->len * prec_complex_bytes(prec);
+    const size_t hi = (size_t)n * w->len * sizeof(double2);
+    const size_t tlo = (size_t)n * w->len * prec_complex_bytes(prec);
+    const size_t thi = (size_t)n * w->len * sizeof(double2);
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void** p, size_t sz) {
+        if (e == cudaSuccess) {
+            e = cudaMalloc(p, sz);
+            if (e == cudaSuccess) w->bytes += sz;
+        }
+    };
+    al(&w->r_lo, lo);
+    al(&w->p_lo, lo);
+    al(&w->Ap_lo, lo);
+    al(&w->x_lo, lo);
+    al(&w->t_lo, tlo);
+    al((void**)&w->b_hi, hi);
+    al((void**)&w->x_hi, hi);
+    al((void**)&w->r_hi, hi);
+    al((void**)&w->t_hi, thi);
+    al((void**)&w->cg, sizeof(CgScalars));
+    al((void**)&w->partials, sizeof(double) * kMaxRedVals * kMaxRedBlocks);
+    al((void**)&w->counter, sizeof(unsigned int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(w->counter, 0, sizeof(unsigned int) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&w->cg_host, sizeof(CgScalars));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        free_workspace(w);
+        return fail(e == cudaErrorMemoryAllocation ? HISQ_ENOMEM : HISQ_ECUDA,
+                    "CG workspace allocation failed: %s", cudaGetErrorString(e));
+    }
+    g->ws.push_back(w);
+    *out = w;
+    return HISQ_OK;
+}
+
+struct Solver {
+    hisq_gauge g;
+    Workspace* w;
+    int n, prec, rpt, full;
+    double mass, mu;
+    double tol2;
+
+    BlasArgs blas() const {
+        BlasArgs b;
+        b.n = n;
+        b.len = w->len;
+        b.red.partials = w->partials;
+        b.red.counter = w->counter;
+        b.cg = w->cg;
+        return b;
+    }
+
+    void* lo_ptr(void* base, int k, long long off = 0) const {
+        return (char*)base + ((size_t)k * w->len + off) * prec_complex_bytes(prec);
+    }
+    double2* hi_ptr(double2* base, int k, long long off = 0) const {
+        return base + (size_t)k * w->len + off;
+    }
+
+    DslashArgs args(int p, int lp) const {
+        DslashArgs a;
+        fill_common(a, g, lp, p, n);
+        a.red.partials = w->partials;
+        a.red.counter = w->counter;
+        a.cg = w->cg;
+        a.tol2 = tol2;
+        return a;
+    }
+
+    // Low-precision A p -> Ap; the last reduction block forms alpha.
+    cudaError_t apply_lo(cudaStream_t s) const {
+        const int ru = g->recon_U, rn = g->recon_N;
+        cudaError_t e;
+        if (!full) {
+            DslashArgs a = args(1, prec);   // t = D_oe p
+            for (int k = 0; k < n; ++k) {
+                a.in[k] = lo_ptr(w->p_lo, k);
+                a.out[k] = lo_ptr(w->t_lo, k);
+            }
+            e = launch_dslash(a, prec, ru, rn, EPI_NONE, rpt, s);
+            if (e != cudaSuccess) return e;
+            DslashArgs b = args(0, prec);   // Ap = 4m^2 p - D_eo t, pAp = Re<p, Ap>
+            b.cx = 4.0 * mass * mass;
+            b.cd = -1.0;
+            b.red_mode = RED_DOT_XW;
+            b.finish = FIN_CG_ALPHA;
+            for (int k = 0; k < n; ++k) {
+                b.in[k] = lo_ptr(w->t_lo, k);
+                b.out[k] = lo_ptr(w->Ap_lo, k);
+                b.x[k] = lo_ptr(w->p_lo, k);
+            }
+            return launch_dslash(b, prec, ru, rn, EPI_X, rpt, s);
+        }
+        // full lattice: y = M(mu) p into t, Ap = M(mu)^dag y, then alpha from Re<p, Ap>
+        const long long hl = w->len_half;
+        for (int par = 0; par < 2; ++par) {
+            DslashArgs a = args(par, prec);
+            set_mu(a, mu);
+            a.cx = 2.0 * mass;
+            a.cd = 1.0;
+            for (int k = 0; k < n; ++k) {
+                a.in[k] = lo_ptr(w->p_lo, k, (1 - par) * hl);
+                a.out[k] = lo_ptr(w->t_lo, k, par * hl);
+                a.x[k] = lo_ptr(w->p_lo, k, par * hl);
+            }
+            e = launch_dslash(a, prec, ru, rn, EPI_X, rpt, s);
+            if (e != cudaSuccess) return e;
+        }
+        for (int par = 0; par < 2; ++par) {
+            DslashArgs a = args(par, prec);
+            set_mu(a, -mu);
+            a.cx = 2.0 * mass;
+            a.cd = -1.0;
+            for (int k = 0; k < n; ++k) {
+                a.in[k] = lo_ptr(w->t_lo, k, (1 - par) * hl);
+                a.out[k] = lo_ptr(w->Ap_lo, k, par * hl);
+                a.x[k] = lo_ptr(w->t_lo, k, par * hl);
+            }
+            e = launch_dslash(a, prec, ru, rn, EPI_X, rpt, s);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_dot_alpha(blas(), prec, w->p_lo, w->Ap_lo, s);
+    }
+
+    // One CG iteration on every active rhs.
+    cudaError_t iterate(cudaStream_t s) const {
+        cudaError_t e = apply_lo(s);
+        if (e == cudaSuccess) e = launch_cg_update_xr(blas(), prec, w->x_lo, w->r_lo, w->p_lo, w->Ap_lo, s);
+        if (e == cudaSuccess) e = launch_cg_update_p(blas(), prec, w->r_lo, w->p_lo, s);
+        return e;
+    }
+
+    // r_hi = b - A x_hi in FP64 with the reliable finish (convergence, scale).
+    cudaError_t true_residual(cudaStream_t s) const {
+        const int f = HISQ_F64;
+        const int r4 = dslash_max_rpt(f);
+        int r64 = 1;
+        while (r64 * 2 <= r4 && n % (r64 * 2) == 0) r64 *= 2;
+        while (n / r64 > 8) r64 *= 2;
+        cudaError_t e;
+        if (!full) {
+            DslashArgs a = args(1, f);   // t = D_oe x
+            for (int k = 0; k < n; ++k) {
+                a.in[k] = hi_ptr(w->x_hi, k);
+                a.out[k] = hi_ptr(w->t_hi, k);
+            }
+            e = launch_dslash(a, f, 18, 18, EPI_NONE, r64, s);
+            if (e != cudaSuccess) return e;
+            DslashArgs b = args(0, f);   // r = b - 4m^2 x + D_eo t
+            b.cx = -4.0 * mass * mass;
+            b.cd = 1.0;
+            b.red_mode = RED_NORM_MAX_W;
+            b.finish = FIN_RELIABLE;
+            for (int k = 0; k < n; ++k) {
+                b.in[k] = hi_ptr(w->t_hi, k);
+                b.out[k] = hi_ptr(w->r_hi, k);
+                b.x[k] = hi_ptr(w->x_hi, k);
+                b.y[k] = hi_ptr(w->b_hi, k);
+            }
+            return launch_dslash(b, f, 18, 18, EPI_XY, r64, s);
+        }
+        const long long hl = w->len_half;
+        for (int par = 0; par < 2; ++par) {   // y = M(mu) x
+            DslashArgs a = args(par, f);
+            set_mu(a, mu);
+            a.cx = 2.0 * mass;
+            a.cd = 1.0;
+            for (int k = 0; k < n; ++k) {
+                a.in[k] = hi_ptr(w->x_hi, k, (1 - par) * hl);
+                a.out[k] = hi_ptr(w->t_hi, k, par * hl);
+                a.x[k] = hi_ptr(w->x_hi, k, par * hl);
+            }
+            e = launch_dslash(a, f, 18, 18, EPI_X, r64, s);
+            if (e != cudaSuccess) return e;
+        }
+        for (int par = 0; par < 2; ++par) {   // r = b - 2m y + D(-mu) y
+            DslashArgs a = args(par, f);
+            set_mu(a, -mu);
+            a.cx = -2.0 * mass;
+            a.cd = 1.0;
+            for (int k = 0; k < n; ++k) {
+                a.in[k] = hi_ptr(w->t_hi, k, (1 - par) * hl);
+                a.out[k] = hi_ptr(w->r_hi, k, par * hl);
+                a.x[k] = hi_ptr(w->t_hi, k, par * hl);
+                a.y[k] = hi_ptr(w->b_hi, k, par * hl);
+            }
+            e = launch_dslash(a, f, 18, 18, EPI_XY, r64, s);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_residual_norm(blas(), w->r_hi, tol2, s);
+    }
+
+    cudaError_t reliable_update(cudaStream_t s) const {
+        cudaError_t e = launch_accum_solution(blas(), prec, w->x_hi, w->x_lo, s);
+        if (e == cudaSuccess) e = true_residual(s);
+        if (e == cudaSuccess) e = launch_reliable_rescale(blas(), prec, w->r_hi, w->r_lo, w->p_lo, 0, s);
+        return e;
+    }
+
+    cudaError_t poll(cudaStream_t s) const {
+        cudaError_t e = cudaMemcpyAsync(w->cg_host, w->cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e;
+    }
+
+    // Run `chunk` iterations, from a captured graph when enabled.
+    hisq_status run_chunk(int chunk, bool graphs, cudaStream_t s) {
+        if (!graphs) {
+            for (int i = 0; i < chunk; ++i) HISQ_CUDA(iterate(s));
+            return HISQ_OK;
+        }
+        GraphKey key{chunk, mass, mu, rpt};
+        auto it = w->graphs.find(key);
+        if (it == w->graphs.end()) {
+            if (w->graphs.size() >= 8) {
+                for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
+                w->graphs.clear();
+            }
+            cudaGraph_t graph = nullptr;
+            HISQ_CUDA(cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = iterate(w->cap_stream);
+            cudaError_t e2 = cudaStreamEndCapture(w->cap_stream, &graph);
+            HISQ_CUDA(e);
+            HISQ_CUDA(e2);
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            HISQ_CUDA(e);
+            it = w->graphs.emplace(key, exec).first;
+        }
+        HISQ_CUDA(cudaGraphLaunch(it->second, s));
+        return HISQ_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const void* const b[],
+                                     void* const x[], int n, double tol, const hisq_cg_params* p,
+                                     hisq_cg_stats* stats, void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(HISQ_EINVAL, "tol must be positive and finite");
+    if (!std::isfinite(mass) || !std::isfinite(mu)) return fail(HISQ_EINVAL, "mass and mu must be finite");
+    if (!b || !x) return fail(HISQ_EINVAL, "NULL pointer array");
+    for (int k = 0; k < n; ++k)
+        if (!b[k] || !x[k]) return fail(HISQ_EINVAL, "NULL source or solution pointer for rhs %d", k);
+    hisq_cg_params prm;
+    hisq_cg_default_params(&prm);
+    if (p) prm = *p;
+    if (!valid_prec(prm.inner_prec)) return fail(HISQ_EINVAL, "unknown inner precision %d", prm.inner_prec);
+    if (prm.inner_prec != HISQ_F64 && prm.inner_prec != g->prec)
+        return fail(HISQ_EINVAL, "inner precision %d needs links stored in that precision (handle has %d)",
+                    prm.inner_prec, g->prec);
+    if (prm.even_odd && mu != 0.0)
+        return fail(HISQ_EINVAL, "mu != 0 needs the full-lattice solve (even_odd = 0)");
+    if (prm.maxiter < 1) return fail(HISQ_EINVAL, "maxiter must be >= 1");
+    if (prm.check_every < 1) prm.check_every = 1;
+    if (prm.reliable_every < 1) prm.reliable_every = 1 << 30;
+    if (!(prm.reliable_delta >= 0.0 && prm.reliable_delta < 1.0))
+        return fail(HISQ_EINVAL, "reliable_delta must be in [0, 1)");
+
+    std::lock_guard<std::mutex> lock(g->mtx);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int full = prm.even_odd ? 0 : 1;
+    Workspace* w = nullptr;
+    hisq_status st = get_workspace(g, n, prm.inner_prec, full, &w);
+    if (st != HISQ_OK) return st;
+
+    Solver sv;
+    sv.g = g;
+    sv.w = w;
+    sv.n = n;
+    sv.prec = prm.inner_prec;
+    sv.full = full;
+    sv.rpt = pick_rpt(g, n, sv.prec, prm.rhs_per_thread);
+    sv.mass = mass;
+    sv.mu = mu;
+    sv.tol2 = tol * tol;
+
+    // sources and initial guess into the FP64 blocks
+    const size_t vec_bytes = (size_t)w->len * sizeof(double2);
+    for (int k = 0; k < n; ++k)
+        HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(w->b_hi, k), b[k], vec_bytes, cudaMemcpyDefault, s));
+    if (prm.use_x0) {
+        for (int k = 0; k < n; ++k)
+            HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(w->x_hi, k), x[k], vec_bytes, cudaMemcpyDefault, s));
+    } else {
+        HISQ_CUDA(cudaMemsetAsync(w->x_hi, 0, vec_bytes * n, s));
+    }
+    HISQ_CUDA(cudaMemsetAsync(w->cg, 0, sizeof(CgScalars), s));
+    HISQ_CUDA(cudaMemsetAsync(w->x_lo, 0, (size_t)n * w->len * prec_complex_bytes(sv.prec), s));
+    HISQ_CUDA(launch_norm_bb(sv.blas(), w->b_hi, s));
+    if (prm.use_x0) {
+        HISQ_CUDA(sv.true_residual(s));
+    } else {
+        HISQ_CUDA(launch_copy_residual(sv.blas(), w->b_hi, w->r_hi, sv.tol2, s));
+    }
+    HISQ_CUDA(launch_reliable_rescale(sv.blas(), sv.prec, w->r_hi, w->r_lo, w->p_lo, 1, s));
+    HISQ_CUDA(sv.poll(s));
+
+    int iters_k[kMaxRhs];
+    for (int k = 0; k < n; ++k) iters_k[k] = 0;
+    int iter = 0, since_rel = 0, reliable = 0;
+    hisq_status result = HISQ_OK;
+    const double d2 = prm.reliable_delta * prm.reliable_delta;
+    auto any_active = [&]() {
+        for (int k = 0; k < n; ++k)
+            if (w->cg_host->active[k]) return true;
+        return false;
+    };
+    while (any_active()) {
+        if (w->cg_host->flags) break;
+        if (iter >= prm.maxiter) {
+            result = HISQ_ENOCONV;
+            break;
+        }
+        int chunk = prm.check_every;
+        if (chunk > prm.reliable_every - since_rel) chunk = prm.reliable_every - since_rel;
+        if (chunk > prm.maxiter - iter) chunk = prm.maxiter - iter;
+        if (chunk < 1) chunk = 1;
+        st = sv.run_chunk(chunk, prm.use_graphs != 0, s);
+        if (st != HISQ_OK) return st;
+        iter += chunk;
+        since_rel += chunk;
+        HISQ_CUDA(sv.poll(s));
+        const CgScalars& h = *w->cg_host;
+        if (h.flags) break;
+        bool need = since_rel >= prm.reliable_every || iter >= prm.maxiter;
+        for (int k = 0; k < n && !need; ++k) {
+            if (!h.active[k]) continue;
+            if (h.rr[k] <= d2 * h.rr_rel[k]) need = true;
+            if (h.rr[k] <= sv.tol2 * h.bb[k] * h.scale[k] * h.scale[k]) need = true;
+        }
+        if (need) {
+            int was[kMaxRhs];
+            for (int k = 0; k < n; ++k) was[k] = h.active[k];
+            HISQ_CUDA(sv.reliable_update(s));
+            HISQ_CUDA(sv.poll(s));
+            ++reliable;
+            since_rel = 0;
+            for (int k = 0; k < n; ++k)
+                if (was[k] && !w->cg_host->active[k]) iters_k[k] = iter;
+        }
+    }
+    if (result == HISQ_ENOCONV) {
+        for (int k = 0; k < n; ++k)
+            if (w->cg_host->active[k]) iters_k[k] = iter;
+    }
+    if (w->cg_host->flags) {
+        // fold what the low-precision solution gathered so far into x
+        HISQ_CUDA(launch_accum_solution(sv.blas(), sv.prec, w->x_hi, w->x_lo, s));
+        HISQ_CUDA(sv.poll(s));
+    }
+    const CgScalars& h = *w->cg_host;
+    if (h.flags & kFlagNaN)
+        result = fail(HISQ_ENAN, "non-finite value in the CG (source or residual)");
+    else if (h.flags & kFlagBreakdown)
+        result = fail(HISQ_EBREAKDOWN, "CG breakdown: <p, A p> <= 0 or not finite");
+    else if (result == HISQ_ENOCONV)
+        fail(HISQ_ENOCONV, "CG did not converge in %d iterations", prm.maxiter);
+    for (int k = 0; k < n; ++k)
+        HISQ_CUDA(cudaMemcpyAsync(x[k], sv.hi_ptr(w->x_hi, k), vec_bytes, cudaMemcpyDefault, s));
+    HISQ_CUDA(cudaStreamSynchronize(s));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        for (int k = 0; k < n; ++k) {
+            stats->iters[k] = iters_k[k];
+            stats->true_rel_res[k] = h.bb[k] > 0 ? std::sqrt(h.rr_true[k] / h.bb[k]) : 0.0;
+        }
+        stats->total_iters = iter;
+        stats->reliable_updates = reliable;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return result;
+}

@@ -1,0 +1,210 @@
+// Internal declarations shared by the CUDA translation units of libhisq.
+//
+// Data layout in HBM (all site-major, so consecutive threads touch
+// consecutive addresses):
+//   links   [parity][mu][complex component c][V_h]  of double2 / float2 / half2
+//           c < 9 (R18), 6 (R12: rows 1-2) or 7 (R14: rows 1-2 and z)
+//   spinors [V_h][3] complex per rhs (the ABI layout), one pointer per rhs
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "hisq.h"
+
+namespace hisq {
+
+constexpr int kMaxRhs = 16;
+constexpr int kMaxRedVals = 2 * kMaxRhs;   // per-rhs norm and max
+constexpr int kMaxRedBlocks = 4096;         // partial-sum slots per reduction
+
+// ---------------------------------------------------------------------------
+// Geometry of the checkerboarded lattice
+// ---------------------------------------------------------------------------
+struct Geom {
+    int L[4];     // Lx, Ly, Lz, Lt
+    int hx;       // Lx / 2 : half sites per x row
+    int vh;       // V / 2
+    int sy;       // half-index stride of y: hx
+    int sz;       // half-index stride of z: hx * Ly
+    int st;       // half-index stride of t: hx * Ly * Lz
+};
+
+// ---------------------------------------------------------------------------
+// Storage precision traits
+// ---------------------------------------------------------------------------
+template <typename S> struct Traits;
+template <> struct Traits<double> {
+    using C = double2;     // stored complex
+    using R = double;      // arithmetic
+    using RC = double2;    // arithmetic complex
+    static constexpr int prec = HISQ_F64;
+};
+template <> struct Traits<float> {
+    using C = float2;
+    using R = float;
+    using RC = float2;
+    static constexpr int prec = HISQ_F32;
+};
+template <> struct Traits<__half> {
+    using C = __half2;
+    using R = float;
+    using RC = float2;
+    static constexpr int prec = HISQ_F16;
+};
+
+__device__ __forceinline__ double2 ld_c(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld_c(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld_c(const __half2* p) { return __half22float2(__ldg(p)); }
+
+// Streaming loads for data read once per launch (links): evict-first hint.
+__device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ld_stream(const __half2* p) {
+    return __half22float2(__ldcs(p));
+}
+
+// The value a store of v through p leaves in memory, in arithmetic precision.
+__device__ __forceinline__ double2 stored_value(double2 v, const double2*) { return v; }
+__device__ __forceinline__ float2 stored_value(float2 v, const float2*) { return v; }
+__device__ __forceinline__ float2 stored_value(float2 v, const __half2*) {
+    return __half22float2(__float22half2_rn(v));
+}
+
+__device__ __forceinline__ void st_c(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void st_c(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void st_c(__half2* p, float2 v) { *p = __float22half2_rn(v); }
+
+// ---------------------------------------------------------------------------
+// Reductions: per-block partials and a last-block finish in fixed order
+// ---------------------------------------------------------------------------
+struct RedScratch {
+    double* partials;        // [kMaxRedVals][kMaxRedBlocks]
+    unsigned int* counter;   // zero between launches; the last block resets it
+};
+
+// CG scalars live on the device so that no iteration needs the host.
+struct CgScalars {
+    double rr[kMaxRhs];        // iterated |r|^2 in the scaled low-precision units
+    double pAp[kMaxRhs];
+    double alpha[kMaxRhs];
+    double beta[kMaxRhs];
+    double rr_rel[kMaxRhs];    // |r|^2 right after the last reliable update (scaled)
+    double bb[kMaxRhs];        // |b|^2, FP64
+    double rr_true[kMaxRhs];   // |b - A x|^2 at the last reliable update, FP64
+    double rmax[kMaxRhs];      // max |component| of that residual
+    double scale[kMaxRhs];     // low-precision vectors hold scale * true vector
+    double scale_old[kMaxRhs];
+    int active[kMaxRhs];       // 1 while rhs k is iterating
+    int flags;                 // kFlagBreakdown | kFlagNaN
+};
+constexpr int kFlagBreakdown = 1;
+constexpr int kFlagNaN = 2;
+
+enum RedMode : int {
+    RED_NONE = 0,
+    RED_DOT_XW = 1,      // Re <x, w> per rhs (x = epilogue input, w = output)
+    RED_NORM_MAX_W = 2   // |w|^2 and max |w_i| per rhs
+};
+
+enum Finish : int {
+    FIN_STORE = 0,       // write the reduced values to red_out
+    FIN_CG_ALPHA = 1,    // pAp -> alpha = rr / pAp (masked)
+    FIN_RELIABLE = 2,    // FP64 true residual -> convergence, next scale
+    FIN_CG_BETA = 3,     // rr' -> beta = rr' / rr (masked)
+    FIN_BB = 4,          // |b|^2 -> bb, active = (bb > 0), scale = 1
+    FIN_RR = 5,          // |r_lo|^2 after a reliable update -> rr, rr_rel
+};
+
+// ---------------------------------------------------------------------------
+// Dslash launch arguments
+// ---------------------------------------------------------------------------
+struct DslashArgs {
+    Geom g;
+    int parity;                         // output parity
+    int nrhs;                           // rhs in this launch
+    const void* U;                      // packed links, [2][4][ncomp][vh]
+    const void* N;
+    const void* in[kMaxRhs];            // opposite-parity inputs
+    void* out[kMaxRhs];                 // outputs
+    const void* x[kMaxRhs];             // epilogue x (output parity), or null
+    const void* y[kMaxRhs];             // epilogue y (output parity), or null
+    double cx, cd;                      // out = [y] + cx * x + cd * (D in)
+    double ft1, bt1, ft3, bt3;          // temporal hop factors e^{+mu}, e^{-mu}, e^{3mu}, e^{-3mu}
+    int has_mu;                         // 1 if any factor differs from 1
+    double r12_inv_scale;               // 1 / s for R12 fat links
+    int red_mode;
+    int finish;
+    double tol2;                        // FIN_RELIABLE: tol^2
+    RedScratch red;
+    double* red_out;                    // [vals] for FIN_STORE
+    CgScalars* cg;                      // for FIN_CG_ALPHA / FIN_RELIABLE
+};
+
+// Epilogue kinds (template parameter of the Dslash kernel)
+enum Epi : int { EPI_NONE = 0, EPI_X = 1, EPI_XY = 2 };
+
+// Dispatch into the instantiated kernels. prec is the spinor and link storage
+// precision; rpt = rhs per thread (1, 2, 4, 8; F64: 1, 2, 4); nrhs must be a
+// multiple of rpt with nrhs / rpt <= 8.
+cudaError_t launch_dslash(const DslashArgs& a, int prec, int ru, int rn, int epi, int rpt,
+                          cudaStream_t s);
+bool dslash_variant_supported(int prec, int ru, int rn, int epi);
+// Largest rhs-per-thread value instantiated for a precision.
+int dslash_max_rpt(int prec);
+
+// ---------------------------------------------------------------------------
+// Link packing (gauge.cu)
+// ---------------------------------------------------------------------------
+// Pack canonical complex128 [4][V][3][3] into [2][4][ncomp][vh] of `prec`,
+// with reconstruct residual max written (as ordered bits) to *err_bits.
+cudaError_t launch_pack_links(const Geom& g, const double2* canon, int prec, int recon,
+                              int hop, double r12_inv_scale, void* out,
+                              unsigned long long* err_bits, cudaStream_t s);
+// Compress to double [4][V][r] and back (ABI helpers).
+cudaError_t launch_compress_links(const Geom& g, const double2* canon, int recon, int hop,
+                                  double r12_inv_scale, double* packed,
+                                  unsigned long long* err_bits, cudaStream_t s);
+cudaError_t launch_reconstruct_links(const Geom& g, const double* packed, int recon,
+                                     int hop, double r12_inv_scale, double2* canon,
+                                     cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// CG vector kernels (blas.cu). Vectors: one contiguous [n][vh*3] complex block.
+// ---------------------------------------------------------------------------
+struct BlasArgs {
+    int n;               // rhs
+    long long len;       // complex elements per rhs (vh * 3)
+    RedScratch red;
+    CgScalars* cg;
+};
+// x_lo += alpha p; r -= alpha Ap; rr' = |r|^2 -> beta = rr'/rr, rr = rr'
+cudaError_t launch_cg_update_xr(const BlasArgs& a, int prec, void* x, void* r,
+                                const void* p, const void* Ap, cudaStream_t s);
+// p = r + beta p
+cudaError_t launch_cg_update_p(const BlasArgs& a, int prec, const void* r, void* p,
+                               cudaStream_t s);
+// x_hi (FP64) += x_lo / scale ; x_lo = 0
+cudaError_t launch_accum_solution(const BlasArgs& a, int prec, double2* x_hi, void* x_lo,
+                                  cudaStream_t s);
+// pAp = Re <p, Ap> -> alpha (full-lattice operator, where the Dslash epilogue
+// does not see p)
+cudaError_t launch_dot_alpha(const BlasArgs& a, int prec, const void* p, const void* Ap,
+                             cudaStream_t s);
+// |r_hi|^2 and max|r_i| with the reliable-update finish
+cudaError_t launch_residual_norm(const BlasArgs& a, const double2* r_hi, double tol2,
+                                 cudaStream_t s);
+// |b|^2 -> bb; active = (bb > 0); scale = 1
+cudaError_t launch_norm_bb(const BlasArgs& a, const double2* b, cudaStream_t s);
+// r_hi = b (x0 = 0) with the reliable-update finish (rr_true, rmax, scale)
+cudaError_t launch_copy_residual(const BlasArgs& a, const double2* b, double2* r_hi,
+                                 double tol2, cudaStream_t s);
+// r_lo = scale * r_hi; p_lo = reset_p ? r_lo : p_lo * scale / scale_old;
+// rr = rr_rel = |r_lo|^2 (active rhs only)
+cudaError_t launch_reliable_rescale(const BlasArgs& a, int prec, const double2* r_hi,
+                                    void* r_lo, void* p_lo, int reset_p, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace hisq

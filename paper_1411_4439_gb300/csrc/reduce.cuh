@@ -1,0 +1,125 @@
+// Block partials plus a last-block finish, in a fixed order (deterministic).
+//
+// Every block writes one partial per reduced value to
+// partials[value * kMaxRedBlocks + blockIdx.x], fences, and bumps a counter;
+// the block that arrives last sums the partials of every value in a fixed
+// order (one warp per value, lane-strided, then a fixed shuffle tree), resets
+// the counter for the next launch and runs the finish logic.
+#pragma once
+
+#include "hisq_internal.cuh"
+
+namespace hisq {
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_max(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Signals arrival of this block; true in the block that arrived last.
+__device__ __forceinline__ bool last_block_arrive(unsigned int* counter, unsigned int nblocks) {
+    __shared__ unsigned int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const unsigned int prev = atomicAdd(counter, 1u);
+        s_last = (prev == nblocks - 1u) ? 1u : 0u;
+    }
+    __syncthreads();
+    return s_last != 0u;
+}
+
+// In the last block: out[v] = sum (or max, when is_max(v)) over slots of
+// partials[v][0 .. nslots). Must be called by all threads of the block.
+template <typename IsMax>
+__device__ __forceinline__ void finish_values(const RedScratch& red, int nvals, int nslots,
+                                              IsMax is_max, double* out_smem) {
+    __threadfence();
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nthreads >> 5;
+    for (int v = warp; v < nvals; v += nwarps) {
+        const double* src = red.partials + (size_t)v * kMaxRedBlocks;
+        const bool mx = is_max(v);
+        double acc = 0.0;
+        for (int i = lane; i < nslots; i += 32) {
+            const double t = __ldcg(src + i);
+            acc = mx ? fmax(acc, t) : acc + t;
+        }
+        acc = mx ? warp_max(acc) : warp_sum(acc);
+        if (lane == 0) out_smem[v] = acc;
+    }
+    if (tid == 0) *red.counter = 0u;
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Finish logic shared by the Dslash and vector kernels
+// ---------------------------------------------------------------------------
+
+// pAp -> alpha_k = rr_k / pAp_k for active rhs; breakdown if pAp <= 0 or not finite.
+__device__ __forceinline__ void finish_cg_alpha(CgScalars* cg, const double* vals, int n) {
+    const int k = threadIdx.x + threadIdx.y * blockDim.x;
+    if (k < n) {
+        const double pAp = vals[k];
+        double alpha = 0.0;
+        if (cg->active[k]) {
+            if (!(pAp > 0.0) || !isfinite(pAp)) {
+                atomicOr(&cg->flags, kFlagBreakdown);
+            } else {
+                alpha = cg->rr[k] / pAp;
+            }
+        }
+        cg->pAp[k] = pAp;
+        cg->alpha[k] = alpha;
+    }
+}
+
+// rr' -> beta_k = rr'_k / rr_k, rr_k = rr'_k for active rhs.
+__device__ __forceinline__ void finish_cg_beta(CgScalars* cg, const double* vals, int n) {
+    const int k = threadIdx.x + threadIdx.y * blockDim.x;
+    if (k < n) {
+        double beta = 0.0;
+        if (cg->active[k]) {
+            const double rr_new = vals[k];
+            if (!isfinite(rr_new)) {
+                atomicOr(&cg->flags, kFlagNaN);
+            } else {
+                beta = rr_new / cg->rr[k];
+                cg->rr[k] = rr_new;
+            }
+        }
+        cg->beta[k] = beta;
+    }
+}
+
+// FP64 true residual (|r|^2 at vals[2k], max|r_i| at vals[2k+1]): record it,
+// retire rhs whose residual meets tol2 * |b|^2, pick the next scale.
+__device__ __forceinline__ void finish_reliable(CgScalars* cg, const double* vals, int n,
+                                                double tol2) {
+    const int k = threadIdx.x + threadIdx.y * blockDim.x;
+    if (k < n) {
+        const double nrm = vals[2 * k], mx = vals[2 * k + 1];
+        cg->rr_true[k] = nrm;
+        cg->rmax[k] = mx;
+        if (!isfinite(nrm)) {
+            atomicOr(&cg->flags, kFlagNaN);
+            cg->active[k] = 0;
+        } else if (cg->active[k] && nrm <= tol2 * cg->bb[k]) {
+            cg->active[k] = 0;
+        }
+        cg->scale_old[k] = cg->scale[k];
+        cg->scale[k] = (mx > 0.0 && isfinite(mx)) ? 1.0 / mx : 1.0;
+    }
+}
+
+}  // namespace hisq

@@ -1,0 +1,296 @@
+"""Python binding of libhisq: the C ABI of include/hisq.h, same names.
+
+Argument marshalling only: every step of the Dslash and the CG runs in the
+CUDA library. Device buffers are torch CUDA tensors (their data pointers are
+passed through), host buffers are numpy arrays or CPU tensors. The stream
+defaults to torch's current CUDA stream. If the compiled library is missing
+every call raises: there is no fallback.
+
+Element types of spinors ([V_h][3] complex per rhs):
+  F64: complex128; F32: complex64; F16: float16 with a trailing (re, im)
+  axis of length 2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libhisq.so")
+
+# status codes
+HISQ_OK, HISQ_EINVAL, HISQ_ERECON, HISQ_ENOCONV = 0, 1, 2, 3
+HISQ_EBREAKDOWN, HISQ_ENAN, HISQ_ECUDA, HISQ_ETIMEOUT, HISQ_ENOMEM = 4, 5, 6, 7, 8
+# precisions and compressions
+HISQ_F64, HISQ_F32, HISQ_F16 = 0, 1, 2
+HISQ_R18, HISQ_R12, HISQ_R14 = 18, 12, 14
+
+STATUS_NAMES = {0: "HISQ_OK", 1: "HISQ_EINVAL", 2: "HISQ_ERECON", 3: "HISQ_ENOCONV",
+                4: "HISQ_EBREAKDOWN", 5: "HISQ_ENAN", 6: "HISQ_ECUDA", 7: "HISQ_ETIMEOUT",
+                8: "HISQ_ENOMEM"}
+MAX_RHS = 16
+
+EXPORTED = ["hisq_version", "hisq_last_error", "hisq_gauge_load", "hisq_gauge_free",
+            "hisq_gauge_info", "hisq_set_dslash_rpt", "hisq_link_compress",
+            "hisq_link_reconstruct", "hisq_dslash", "hisq_dslash_ex", "hisq_mdagm",
+            "hisq_cg_default_params", "hisq_cg_solve"]
+
+
+class HisqError(RuntimeError):
+    def __init__(self, status: int, message: str, stats=None):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.stats = stats
+
+
+class hisq_cg_params(ctypes.Structure):
+    _fields_ = [("maxiter", ctypes.c_int), ("reliable_every", ctypes.c_int),
+                ("reliable_delta", ctypes.c_double), ("inner_prec", ctypes.c_int),
+                ("use_x0", ctypes.c_int), ("even_odd", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("rhs_per_thread", ctypes.c_int)]
+
+
+class hisq_cg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int * MAX_RHS), ("total_iters", ctypes.c_int),
+                ("reliable_updates", ctypes.c_int),
+                ("true_rel_res", ctypes.c_double * MAX_RHS), ("seconds", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """The loaded libhisq (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise HisqError(HISQ_ECUDA, f"{LIB_PATH} is missing; build it with "
+                        "`python -m paper_1411_4439_gb300.build_lib`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ip, c_int, c_double = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double
+    sig = {
+        "hisq_version": (c_int, []),
+        "hisq_last_error": (ctypes.c_char_p, []),
+        "hisq_gauge_load": (c_int, [ip, vp, vp, c_int, c_int, c_int, c_int, c_double, vp,
+                                    ctypes.POINTER(vp)]),
+        "hisq_gauge_free": (c_int, [vp]),
+        "hisq_gauge_info": (c_int, [vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_size_t)]),
+        "hisq_set_dslash_rpt": (c_int, [vp, c_int]),
+        "hisq_link_compress": (c_int, [ip, vp, c_int, vp, ctypes.POINTER(c_double), vp]),
+        "hisq_link_reconstruct": (c_int, [ip, vp, c_int, vp, vp]),
+        "hisq_dslash": (c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int, c_int, vp]),
+        "hisq_dslash_ex": (c_int, [vp, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int,
+                                   c_int, vp]),
+        "hisq_mdagm": (c_int, [vp, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int, vp]),
+        "hisq_cg_default_params": (None, [ctypes.POINTER(hisq_cg_params)]),
+        "hisq_cg_solve": (c_int, [vp, c_double, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
+                                  c_double, ctypes.POINTER(hisq_cg_params),
+                                  ctypes.POINTER(hisq_cg_stats), vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, stats=None):
+    if status != HISQ_OK:
+        msg = library().hisq_last_error().decode(errors="replace")
+        raise HisqError(status, msg, stats)
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(buf) -> int:
+    """Address of a torch tensor or numpy array (must be contiguous)."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffer must be C-contiguous")
+        return buf.ctypes.data
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr()
+    if isinstance(buf, int):
+        return buf
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _is_device(buf) -> bool:
+    return hasattr(buf, "is_cuda") and bool(buf.is_cuda)
+
+
+def _stream_handle(stream, *bufs) -> int | None:
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    if any(_is_device(b) for b in bufs):
+        return int(_torch().cuda.current_stream().cuda_stream)
+    return None
+
+
+def _ptr_array(bufs):
+    arr = (ctypes.c_void_p * len(bufs))()
+    for i, b in enumerate(bufs):
+        arr[i] = _ptr(b)
+    return arr
+
+
+def _lattice(L):
+    L = [int(a) for a in L]
+    if len(L) != 4:
+        raise ValueError("L must have 4 extents")
+    return (ctypes.c_int * 4)(*L)
+
+
+# ---------------------------------------------------------------------------
+# C ABI, same names
+# ---------------------------------------------------------------------------
+
+def hisq_version() -> int:
+    return library().hisq_version()
+
+
+def hisq_last_error() -> str:
+    return library().hisq_last_error().decode(errors="replace")
+
+
+@dataclass
+class Gauge:
+    """Owner of a hisq_gauge handle; free with hisq_gauge_free or `with`."""
+    handle: int
+    L: tuple
+    prec: int
+    recon_U: int
+    recon_N: int
+    _freed: bool = field(default=False, repr=False)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        hisq_gauge_free(self)
+
+    def __del__(self):
+        try:
+            hisq_gauge_free(self)
+        except Exception:
+            pass
+
+
+def hisq_gauge_load(L, U, N, prec=HISQ_F32, recon_U=HISQ_R18, recon_N=HISQ_R18,
+                    recon_tol=1e-10, stream=None) -> Gauge:
+    """Load canonical complex128 [4][V][3][3] links (device tensor or host array)."""
+    on_dev = _is_device(U)
+    if on_dev != _is_device(N):
+        raise ValueError("U and N must both be on the device or both on the host")
+    for a in (U, N):
+        dt = getattr(a, "dtype", None)
+        if str(dt) not in ("complex128", "torch.complex128"):
+            raise TypeError("links must be complex128")
+    h = ctypes.c_void_p()
+    st = library().hisq_gauge_load(_lattice(L), _ptr(U), _ptr(N), int(on_dev), int(prec),
+                                   int(recon_U), int(recon_N), float(recon_tol),
+                                   _stream_handle(stream, U, N), ctypes.byref(h))
+    _check(st)
+    return Gauge(h.value, tuple(int(a) for a in L), int(prec), int(recon_U), int(recon_N))
+
+
+def hisq_gauge_free(g: Gauge) -> None:
+    if g is None or g._freed:
+        return
+    g._freed = True
+    _check(library().hisq_gauge_free(g.handle))
+
+
+def hisq_gauge_info(g: Gauge) -> dict:
+    L = (ctypes.c_int * 4)()
+    prec, ru, rn = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nbytes = ctypes.c_size_t()
+    _check(library().hisq_gauge_info(g.handle, L, ctypes.byref(prec), ctypes.byref(ru),
+                                     ctypes.byref(rn), ctypes.byref(nbytes)))
+    return dict(L=tuple(L), prec=prec.value, recon_U=ru.value, recon_N=rn.value,
+                device_bytes=nbytes.value)
+
+
+def hisq_set_dslash_rpt(g: Gauge, rpt: int) -> None:
+    _check(library().hisq_set_dslash_rpt(g.handle, int(rpt)))
+
+
+def hisq_link_compress(L, links, recon, packed, stream=None) -> float:
+    """Device complex128 [4][V][3][3] -> device float64 [4][V][recon]; returns max error."""
+    err = ctypes.c_double()
+    _check(library().hisq_link_compress(_lattice(L), _ptr(links), int(recon), _ptr(packed),
+                                        ctypes.byref(err), _stream_handle(stream, links)))
+    return err.value
+
+
+def hisq_link_reconstruct(L, packed, recon, links, stream=None) -> None:
+    _check(library().hisq_link_reconstruct(_lattice(L), _ptr(packed), int(recon), _ptr(links),
+                                           _stream_handle(stream, packed)))
+
+
+def hisq_dslash(g: Gauge, v, w, parity: int, prec: int, stream=None) -> None:
+    """w[k] = D_{p,1-p} v[k] (Eq. 3, Eq. 4); v, w lists of device tensors."""
+    hisq_dslash_ex(g, 0.0, v, w, parity, prec, stream)
+
+
+def hisq_dslash_ex(g: Gauge, mu: float, v, w, parity: int, prec: int, stream=None) -> None:
+    if len(v) != len(w):
+        raise ValueError("v and w need the same number of rhs")
+    _check(library().hisq_dslash_ex(g.handle, float(mu), _ptr_array(v), _ptr_array(w), len(v),
+                                    int(parity), int(prec), _stream_handle(stream, *v)))
+
+
+def hisq_mdagm(g: Gauge, mass: float, v, w, prec: int, stream=None) -> None:
+    """w[k] = (4 m^2 - D_eo D_oe) v[k] on even sites."""
+    if len(v) != len(w):
+        raise ValueError("v and w need the same number of rhs")
+    _check(library().hisq_mdagm(g.handle, float(mass), _ptr_array(v), _ptr_array(w), len(v),
+                                int(prec), _stream_handle(stream, *v)))
+
+
+def hisq_cg_default_params() -> hisq_cg_params:
+    p = hisq_cg_params()
+    library().hisq_cg_default_params(ctypes.byref(p))
+    return p
+
+
+def cg_params(**kw) -> hisq_cg_params:
+    """Defaults of the library with the given fields replaced."""
+    p = hisq_cg_default_params()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"hisq_cg_params has no field {k}")
+        setattr(p, k, v)
+    return p
+
+
+def hisq_cg_solve(g: Gauge, mass: float, mu: float, b, x, tol: float, params=None,
+                  stream=None) -> hisq_cg_stats:
+    """Solve the normal equations per rhs; b, x lists of complex128 buffers.
+
+    Raises HisqError on any status but HISQ_OK (the stats ride on the error).
+    """
+    if len(b) != len(x):
+        raise ValueError("b and x need the same number of rhs")
+    stats = hisq_cg_stats()
+    p = params if params is not None else hisq_cg_default_params()
+    st = library().hisq_cg_solve(g.handle, float(mass), float(mu), _ptr_array(b), _ptr_array(x),
+                                 len(b), float(tol), ctypes.byref(p), ctypes.byref(stats),
+                                 _stream_handle(stream, *b, *x))
+    _check(st, stats)
+    return stats

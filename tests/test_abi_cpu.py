@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads and exports every symbol include/hisq.h declares.
+
+No GPU needed: only calls that fail argument validation before touching CUDA
+are made.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT, lib_built
+
+HEADER = os.path.join(ROOT, "include", "hisq.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hisq_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = lib_built()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("hisq_gauge_load", "hisq_dslash", "hisq_dslash_ex", "hisq_cg_solve",
+                 "hisq_link_compress", "hisq_link_reconstruct", "hisq_mdagm"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in hisq.h but not exported"
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_1411_4439_gb300.hisq as B
+    assert sorted(B.EXPORTED) == declared_functions()
+    for name in declared_functions():
+        assert callable(getattr(B, name))
+
+
+def test_version_and_defaults_without_gpu(lib):
+    import paper_1411_4439_gb300 as H
+    assert H.hisq_version() >= 10000
+    p = H.hisq_cg_default_params()
+    assert (p.maxiter, p.reliable_every, p.inner_prec, p.even_odd) == (100000, 50, H.HISQ_F32, 1)
+    assert abs(p.reliable_delta - 0.1) < 1e-15
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 5), (2, 4, 4, 4), (4, 4, 4, 0)])
+def test_bad_extents_rejected_before_cuda(L):
+    import numpy as np
+    import paper_1411_4439_gb300 as H
+    U = np.zeros((4, 4, 4, 4, 4, 3, 3), dtype=np.complex128)
+    with pytest.raises(H.HisqError) as e:
+        H.hisq_gauge_load(L, U, U)
+    assert e.value.status == H.hisq.HISQ_EINVAL
+    assert "extent" in str(e.value)
+
+
+def test_bad_modes_rejected(lib):
+    import numpy as np
+    import paper_1411_4439_gb300 as H
+    U = np.zeros((4, 4, 4, 4, 4, 3, 3), dtype=np.complex128)
+    for kw in (dict(recon_N=12), dict(recon_U=8), dict(prec=7),
+               dict(prec=H.HISQ_F64, recon_N=14)):
+        with pytest.raises(H.HisqError) as e:
+            H.hisq_gauge_load((4, 4, 4, 4), U, U, **kw)
+        assert e.value.status == H.hisq.HISQ_EINVAL
+
+
+def test_null_handle_rejected(lib):
+    assert lib.hisq_gauge_free(None) == 0
+    f = lib.hisq_dslash
+    f.restype = ctypes.c_int
+    assert f(None, None, None, 1, 0, 1, None) == 1   # HISQ_EINVAL

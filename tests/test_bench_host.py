@@ -1,0 +1,67 @@
+"""Host-side logic of bench.py: byte accounting and the multi-rank timing reduction.
+
+The multi-GPU path shards independent rhs bundles across ranks (weak
+scaling, no data-path collective); the only collectives are a barrier and
+the max-over-ranks of the step time. They run here as two gloo ranks on CPU.
+"""
+import os
+import socket
+
+import pytest
+
+import bench
+from oracle import hisq_oracle as O
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("fu,fn,sl,ss", [(18, 18, 8, 8), (18, 14, 4, 4), (18, 14, 2, 2), (12, 14, 2, 2)])
+def test_algorithmic_bytes_match_oracle_model(n, fu, fn, sl, ss):
+    assert bench.dslash_bytes_per_site(n, fu, fn, sl, ss) == O.dslash_bytes_algorithmic(n, fu, fn, sl, ss)
+
+
+def test_survey_byte_table_values():
+    # bytes per output site: FP32 18/14 at n = 8 is 1408, FP16 12/14 at n = 1 is 440
+    assert bench.dslash_bytes_per_site(8, 18, 14, 4, 4) == 1408
+    assert bench.dslash_bytes_per_site(1, 12, 14, 2, 2) == 440
+    assert bench.dslash_bytes_per_site(16, 18, 18, 8, 8) == 3840
+
+
+def test_rank_bundles_are_distinct():
+    seeds = {bench.source_seed_for_rank(r) for r in range(8)}
+    assert len(seeds) == 8
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        bench.barrier(world)
+        t = bench.reduce_max(1.0 + rank, world)
+        q.put((rank, t))
+        bench.barrier(world)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_max_reduction_over_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    assert got == {0: 2.0, 1: 2.0}

@@ -1,0 +1,221 @@
+"""GPU conjugate gradient against the FP64 oracle.
+
+Targets: true relative residual <= 1e-10 recomputed by the oracle from the
+GPU solution, and solution relative error <= 1e-8 against an oracle CG
+driven to 1e-13 (on lattices where the oracle solve takes seconds).
+"""
+import numpy as np
+import pytest
+
+import hisq_inputs as gen
+from oracle import hisq_oracle as O
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def solve(H, L, U, N, b, mass, tol=1e-10, prec=1, ru=18, rn=14, mu=0.0, host=False, full=False,
+          **kw):
+    import torch
+    g = H.hisq_gauge_load(L, dev(U), dev(N), prec=max(prec, 1) if prec else 0,
+                          recon_U=ru if prec else 18, recon_N=rn if prec else 18)
+    try:
+        n = b.shape[0]
+        if host:
+            bt = [np.ascontiguousarray(b[k]) for k in range(n)]
+            xt = [np.zeros_like(b[k]) for k in range(n)]
+        else:
+            bt = [dev(b[k]) for k in range(n)]
+            xt = [torch.zeros_like(t) for t in bt]
+        if "even_odd" not in kw:
+            kw["even_odd"] = 0 if (mu != 0 or full) else 1
+        p = H.cg_params(inner_prec=prec, **kw)
+        stats = H.hisq_cg_solve(g, mass, mu, bt, xt, tol, p)
+        x = np.stack([t if host else t.cpu().numpy() for t in xt])
+        return x, stats
+    finally:
+        H.hisq_gauge_free(g)
+
+
+def oracle_solution(U, N, L, b, m, mu=None):
+    if mu is None:
+        A = lambda q: O.apply_Ae(U, N, q, L, m)
+    else:
+        A = lambda q: O.apply_MdagM(U, N, q, m, mu)
+    x, _ = O.cg(A, b, tol=1e-13)
+    return x, A
+
+
+def test_config0_fp64_single_rhs(gpu_lib):
+    """8^4, FP64, 1 rhs, m = 0.05, complex Z2 source with seed 0, tol 1e-10."""
+    H = gpu_lib
+    L, m = (8, 8, 8, 8), 0.05
+    U, N = gen.hisq_links(L, seed=0)
+    b = gen.z2_source(L, 1, seed=0)
+    x, st = solve(H, L, U, N, b, m, prec=0)
+    xo, A = oracle_solution(U, N, L, b, m)
+    assert O.true_relative_residual(A, x, b)[0] <= 1e-10
+    assert rel_l2(x, xo) <= 1e-8
+    assert st.true_rel_res[0] <= 1e-10 and st.iters[0] > 10
+
+
+@pytest.mark.parametrize("prec,ru,rn", [(1, 18, 14), (1, 18, 18), (1, 12, 14), (2, 18, 14), (2, 14, 14)])
+def test_mixed_precision_multi_rhs(gpu_lib, prec, ru, rn):
+    H = gpu_lib
+    L, m, n = (4, 6, 8, 10), 0.02, 4
+    U, N = gen.hisq_links(L, seed=1)
+    b = gen.z2_source(L, n, seed=2) if prec == 1 else gen.gaussian_source(L, n, seed=2)
+    x, st = solve(H, L, U, N, b, m, prec=prec, ru=ru, rn=rn)
+    xo, A = oracle_solution(U, N, L, b, m)
+    res = O.true_relative_residual(A, x, b)
+    assert np.all(res <= 1e-10), res
+    for k in range(n):
+        assert rel_l2(x[k], xo[k]) <= 1e-8
+        assert abs(st.true_rel_res[k] - res[k]) <= 1e-11
+    assert st.reliable_updates >= 1
+
+
+def test_config1_multi_rhs_fp32_reliable_every_50(gpu_lib):
+    """Multi-rhs FP32 CG with FP64 reliable updates every 50 iterations, n = 1, 2, 4, 8."""
+    H = gpu_lib
+    L, m = (8, 8, 8, 8), 0.01
+    U, N = gen.hisq_links(L, seed=1)
+    b8 = gen.z2_source(L, 8, seed=2)
+    xo, A = oracle_solution(U, N, L, b8, m)
+    for n in (1, 2, 4, 8):
+        x, st = solve(H, L, U, N, b8[:n], m, prec=1, reliable_every=50)
+        res = O.true_relative_residual(A, x, b8[:n])
+        assert np.all(res <= 1e-10), (n, res)
+        for k in range(n):
+            assert rel_l2(x[k], xo[k]) <= 1e-8
+        assert st.reliable_updates >= st.total_iters // 50
+
+
+def test_full_lattice_solve_with_chemical_potential(gpu_lib):
+    H = gpu_lib
+    L, m, mu = (4, 4, 4, 6), 0.1, 0.1
+    U, N = gen.hisq_links(L, seed=5)
+    n = 2
+    be = gen.z2_source(L, n, seed=6)
+    bo = gen.z2_source(L, n, seed=7)
+    b_blocked = np.concatenate([be, bo], axis=1)             # [n][2 V_h][3]
+    b_full = O.to_full(be, L, 0) + O.to_full(bo, L, 1)
+    for prec in (0, 1):
+        x_blocked, st = solve(H, L, U, N, b_blocked, m, prec=prec, mu=mu)
+        vh = be.shape[1]
+        x_full = O.to_full(x_blocked[:, :vh], L, 0) + O.to_full(x_blocked[:, vh:], L, 1)
+        xo, A = oracle_solution(U, N, L, b_full, m, mu=mu)
+        assert np.all(O.true_relative_residual(A, x_full, b_full) <= 1e-10)
+        assert rel_l2(x_full, xo) <= 1e-8
+
+
+def test_full_lattice_at_zero_mu_equals_even_odd(gpu_lib):
+    H = gpu_lib
+    L, m = (4, 6, 8, 10), 0.05
+    U, N = gen.hisq_links(L, seed=8)
+    be = gen.z2_source(L, 1, seed=9)
+    x_eo, _ = solve(H, L, U, N, be, m, prec=0)
+    blocked = np.concatenate([be, np.zeros_like(be)], axis=1)
+    x_fl, _ = solve(H, L, U, N, blocked, m, prec=0, full=True)
+    vh = be.shape[1]
+    assert rel_l2(x_fl[:, :vh], x_eo) < 1e-9
+    assert np.linalg.norm(x_fl[:, vh:]) < 1e-9 * np.linalg.norm(x_eo)
+
+
+def test_zero_source_and_eigenvector_source_in_one_bundle(gpu_lib):
+    H = gpu_lib
+    L, m = (8, 8, 8, 8), 0.05
+    c1, c3 = 9 / 8, -1 / 24
+    U, N = gen.free_field_links(L, c1, c3)
+    Lt, Lz, Ly, Lx = O.grid_shape(L)
+    t, z, y, x = np.meshgrid(np.arange(Lt), np.arange(Lz), np.arange(Ly), np.arange(Lx), indexing="ij")
+    p = [2 * np.pi / Lx, 0.0, 4 * np.pi / Lz, 3 * np.pi / Lt]
+    wave = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))[None, ..., None] * np.array([1, 0.5, 0.25j])
+    ve = O.to_half(wave, L, 0)[0]
+    lam = 4 * m * m + sum((2 * c1 * np.sin(q) + 2 * c3 * np.sin(3 * q)) ** 2 for q in p)
+    b = np.stack([ve, np.zeros_like(ve), gen.z2_source(L, 1, seed=3)[0]])
+    for prec in (0, 1):
+        xg, st = solve(H, L, U, N, b, m, prec=prec, ru=18, rn=18)
+        assert rel_l2(xg[0], ve / lam) < 1e-9
+        assert np.all(xg[1] == 0) and st.iters[1] == 0
+        assert st.iters[0] <= 12 and st.iters[2] > st.iters[0]
+
+
+def test_host_buffers_and_initial_guess(gpu_lib):
+    H = gpu_lib
+    L, m = (4, 6, 8, 10), 0.05
+    U, N = gen.hisq_links(L, seed=11)
+    b = gen.z2_source(L, 2, seed=12)
+    x_host, st = solve(H, L, U, N, b, m, prec=1, host=True)
+    xo, A = oracle_solution(U, N, L, b, m)
+    assert np.all(O.true_relative_residual(A, x_host, b) <= 1e-10)
+    # restarting from the solution needs no iteration
+    import torch
+    g = H.hisq_gauge_load(L, dev(U), dev(N), prec=1, recon_U=18, recon_N=14)
+    try:
+        bt = [dev(b[k]) for k in range(2)]
+        xt = [dev(x_host[k]) for k in range(2)]
+        st2 = H.hisq_cg_solve(g, m, 0.0, bt, xt, 1e-10, H.cg_params(use_x0=1))
+        assert st2.total_iters == 0
+        assert rel_l2(np.stack([t.cpu().numpy() for t in xt]), x_host) < 1e-15
+    finally:
+        H.hisq_gauge_free(g)
+
+
+def test_graph_replay_is_bitwise_identical_to_launches(gpu_lib):
+    H = gpu_lib
+    L, m = (8, 8, 8, 8), 0.02
+    U, N = gen.hisq_links(L, seed=13)
+    b = gen.z2_source(L, 4, seed=14)
+    x1, s1 = solve(H, L, U, N, b, m, prec=1, use_graphs=1)
+    x2, s2 = solve(H, L, U, N, b, m, prec=1, use_graphs=0)
+    assert np.array_equal(x1, x2)
+    assert s1.total_iters == s2.total_iters
+
+
+def test_bundle_equals_single_rhs_solves(gpu_lib):
+    H = gpu_lib
+    L, m = (4, 6, 8, 10), 0.03
+    U, N = gen.hisq_links(L, seed=15)
+    b = gen.z2_source(L, 4, seed=16)
+    xb, _ = solve(H, L, U, N, b, m, prec=1)
+    for k in range(4):
+        xk, _ = solve(H, L, U, N, b[k:k + 1], m, prec=1)
+        assert rel_l2(xk[0], xb[k]) < 1e-8
+
+
+def test_errors_surface_as_status(gpu_lib):
+    H = gpu_lib
+    L, m = (4, 4, 4, 4), 0.01
+    U, N = gen.hisq_links(L, seed=17)
+    b = gen.z2_source(L, 1, seed=18)
+    with pytest.raises(H.HisqError) as e:
+        solve(H, L, U, N, b, m, prec=1, maxiter=5)
+    assert e.value.status == H.hisq.HISQ_ENOCONV
+    assert e.value.stats.total_iters == 5
+    bn = b.copy()
+    bn[0, 7, 1] = np.nan
+    with pytest.raises(H.HisqError) as e:
+        solve(H, L, U, N, bn, m, prec=1)
+    assert e.value.status == H.hisq.HISQ_ENAN
+    with pytest.raises(H.HisqError) as e:
+        solve(H, L, U, N, b, m, prec=1, mu=0.1, even_odd=1)
+    assert e.value.status == H.hisq.HISQ_EINVAL
+
+
+def test_full_size_config1_true_residual(gpu_lib):
+    """32^3x8, n = 8, FP32 (U r18, N r14), m = 0.01, reliable every 50, tol 1e-10."""
+    H = gpu_lib
+    L, m = (32, 32, 32, 8), 0.01
+    U, N = gen.hisq_links(L, seed=1)
+    b = gen.z2_source(L, 8, seed=2)
+    x, st = solve(H, L, U, N, b, m, prec=1, reliable_every=50)
+    res = O.true_relative_residual(lambda q: O.apply_Ae(U, N, q, L, m), x, b)
+    assert np.all(res <= 1e-10), res
+    for k in range(8):
+        assert abs(st.true_rel_res[k] - res[k]) <= 1e-11
