@@ -72,6 +72,11 @@ enum { HISQ_F64 = 0, HISQ_F32 = 1, HISQ_F16 = 2 };
 typedef int hisq_recon;
 enum { HISQ_R18 = 18, HISQ_R12 = 12, HISQ_R14 = 14 };
 
+/* Spinor layout of one rhs on one parity: AoS [V_h][3] (colour fastest) or
+ * SoA [3][V_h] (site fastest, one plane per colour). */
+typedef int hisq_layout;
+enum { HISQ_AOS = 0, HISQ_SOA = 1 };
+
 typedef struct hisq_gauge_s* hisq_gauge;
 
 /* Library version, major*10000 + minor*100 + patch. */
@@ -120,10 +125,12 @@ hisq_status hisq_gauge_info(hisq_gauge g, int L[4], hisq_prec* prec,
                             size_t* device_bytes);
 
 /*
- * Tuning: Dslash right-hand sides per thread for this handle (0 = automatic,
- * else 1, 2, 4 or 8; values that do not divide n fall back to automatic).
+ * Tuning of the Dslash thread mapping for this handle: rhs handled per
+ * thread (1, 2, 4, 8; FP64: 1, 2, 4) and the minimum resident blocks per SM
+ * the kernel is compiled for (register budget). 0 = automatic. Pairs that
+ * are not built, or rpt values that do not divide n, fall back to automatic.
  */
-hisq_status hisq_set_dslash_rpt(hisq_gauge g, int rpt);
+hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_blocks);
 
 /*
  * Compress a canonical link field to `r` reals per link (R18/R14/R12, same
@@ -148,15 +155,17 @@ hisq_status hisq_link_reconstruct(const int L[4], const void* packed,
  *   n            1..16.
  *   spinor_prec  F64 uses the FP64 R18 links; F32 and F16 use the handle's
  *                storage copy, which must then have that same precision.
- * hisq_dslash_ex adds a chemical potential mu on the temporal hops: forward
- * one-hop x e^{+mu}, backward one-hop x e^{-mu}, forward Naik x e^{+3mu},
- * backward Naik x e^{-3mu}. Asynchronous on `stream`.
+ * hisq_dslash uses the AoS layout. hisq_dslash_ex takes the spinor layout and
+ * adds a chemical potential mu on the temporal hops: forward one-hop
+ * x e^{+mu}, backward one-hop x e^{-mu}, forward Naik x e^{+3mu}, backward
+ * Naik x e^{-3mu}. Asynchronous on `stream`.
  */
 hisq_status hisq_dslash(hisq_gauge g, const void* const v[], void* const w[],
                         int n, int parity, hisq_prec spinor_prec, void* stream);
 hisq_status hisq_dslash_ex(hisq_gauge g, double mu, const void* const v[],
                            void* const w[], int n, int parity,
-                           hisq_prec spinor_prec, void* stream);
+                           hisq_prec spinor_prec, hisq_layout layout,
+                           void* stream);
 
 /*
  * Even-odd normal operator of M = 2m + D at mu = 0:
@@ -169,6 +178,46 @@ hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v[],
                        void* const w[], int n, hisq_prec spinor_prec,
                        void* stream);
 
+/*
+ * Full-lattice fermion matrix M(mu) = 2m + D(mu) and its relatives on
+ * parity-blocked vectors [2][V_h][3] (even half first):
+ *   HISQ_OP_M      w = M(mu) v
+ *   HISQ_OP_MDAG   w = M(mu)^dag v = 2m v - D(-mu) v
+ *   HISQ_OP_DM_DMU w = dM/dmu v: the temporal hops only, with factors
+ *                  +e^{mu}, +e^{-mu} (one-hop) and +3e^{3mu}, +3e^{-3mu} (Naik)
+ *                  on U v(x+t), U^dag v(x-t), N v(x+3t), N^dag v(x-3t).
+ * M(mu) is the matrix whose mu-derivatives enter the stochastic traces of
+ * Eq. 2. v and w: n device pointers each; w must not overlap any v.
+ * Asynchronous on `stream`.
+ */
+enum { HISQ_OP_M = 0, HISQ_OP_MDAG = 1, HISQ_OP_DM_DMU = 2 };
+hisq_status hisq_apply_m(hisq_gauge g, double mass, double mu, int op,
+                         const void* const v[], void* const w[], int n,
+                         hisq_prec spinor_prec, void* stream);
+
+/*
+ * Link force for gradients of a solve. For FP64 parity-blocked vectors a_k,
+ * b_k ([2][V_h][3] complex128, device) accumulates into `out` (device,
+ * complex128 [4][V][3][3], canonical link layout)
+ *   out[mu][x] += coef * sum_k [ f a_k(x) b_k(x+hop mu)^dag
+ *                               - (1/f) b_k(x) a_k(x+hop mu)^dag ]
+ * with f = e^{hop mu} on temporal links (1 otherwise); hop = 1 for the fat
+ * links U, 3 for the Naik links N. This is the derivative (d/dRe + i d/dIm)
+ * of Re sum_k a_k^dag D(mu) b_k with respect to each link. Asynchronous.
+ */
+hisq_status hisq_link_force(hisq_gauge g, double mu, int hop, const void* const a[],
+                            const void* const b[], int n, double coef, void* out,
+                            void* stream);
+
+/*
+ * out[2k] + i out[2k+1] = <a_k, b_k> = sum_i conj(a_k[i]) b_k[i] over `len`
+ * complex128 numbers, in FP64 with a fixed summation order. a, b: n device
+ * pointers; out: host array of 2n doubles. Uses reduction scratch owned by
+ * the handle. Synchronises `stream`.
+ */
+hisq_status hisq_cdot(hisq_gauge g, const void* const a[], const void* const b[], int n,
+                      long long len, double* out, void* stream);
+
 /* CG parameters; hisq_cg_default_params fills the defaults noted below. */
 typedef struct {
     int maxiter;           /* iteration cap (100000) */
@@ -180,6 +229,7 @@ typedef struct {
     int check_every;       /* host convergence poll interval (10) */
     int use_graphs;        /* 1: replay iterations from a captured CUDA graph (1) */
     int rhs_per_thread;    /* Dslash rhs per thread: 0 = auto, else 1/2/4/8 */
+    hisq_layout spinor_layout; /* layout of the CG's internal vectors (HISQ_SOA) */
 } hisq_cg_params;
 
 typedef struct {

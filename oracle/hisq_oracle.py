@@ -187,6 +187,21 @@ def apply_MdagM(U, N, v, mass: float, mu_chem: float = 0.0):
     return apply_Mdag(U, N, apply_M(U, N, v, mass, mu_chem), mass, mu_chem)
 
 
+def apply_dM_dmu(U, N, v, mu_chem: float = 0.0):
+    """dM/dmu v = dD/dmu v: the temporal terms of Eq. 3 differentiated in mu.
+
+    d/dmu of  e^{mu} U_3(x) v(x+t) - e^{-mu} U_3(x-t)^dag v(x-t)
+            + e^{3mu} N_3(x) v(x+3t) - e^{-3mu} N_3(x-3t)^dag v(x-3t).
+    """
+    v = np.asarray(v, dtype=COMPLEX)
+    mu = 3
+    w = np.exp(mu_chem) * _matvec(U[mu], shift(v, mu, +1, 1))
+    w += np.exp(-mu_chem) * _matvec(_dagger(shift(U[mu], mu, -1, 0)), shift(v, mu, -1, 1))
+    w += 3.0 * np.exp(3.0 * mu_chem) * _matvec(N[mu], shift(v, mu, +3, 1))
+    w += 3.0 * np.exp(-3.0 * mu_chem) * _matvec(_dagger(shift(N[mu], mu, -3, 0)), shift(v, mu, -3, 1))
+    return w
+
+
 def apply_Ae(U, N, v_half, L, mass: float):
     """Even-odd normal operator A_e v = 4m^2 v - D_eo D_oe v on even sites."""
     t_odd = dslash_parity(U, N, v_half, L, 1)

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) update_xr_kernel(BlasArgs a, void* x
     const long long nch = a.len / N;
     const long long off = (long long)k * nch;
     R val[1] = {(R)0};
-    if (a.cg->active[k]) {
+    if (moving(a.cg, k)) {
         const R alpha = (R)a.cg->alpha[k];
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nch;
              i += (long long)gridDim.x * blockDim.x) {
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) update_p_kernel(BlasArgs a, const vo
     using RC = typename CxOf<R>::T;
     constexpr int N = V::N;
     const int k = blockIdx.y;
-    if (!a.cg->active[k]) return;
+    if (!moving(a.cg, k)) return;
     const long long nch = a.len / N;
     const long long off = (long long)k * nch;
     const R beta = (R)a.cg->beta[k];
@@ -231,6 +231,10 @@ __global__ void __launch_bounds__(kThreads) norm_bb_kernel(BlasArgs a, const dou
             a.cg->alpha[t] = 0.0;
             a.cg->beta[t] = 0.0;
         }
+        if (t == 0) {
+            a.cg->freeze2 = a.freeze2;
+            a.cg->alpha_max = a.alpha_max;
+        }
         if (t == 0) a.cg->flags = isfinite(s_vals[0]) ? a.cg->flags : (a.cg->flags | kFlagNaN);
     }
 }
@@ -268,6 +272,7 @@ __global__ void __launch_bounds__(kThreads) rescale_kernel(BlasArgs a, const dou
     const long long off = (long long)k * nch;
     R val[1] = {(R)0};
     if (a.cg->active[k]) {
+        const bool reset = reset_p != 0;
         const double sc = a.cg->scale[k];
         const R ratio = (R)(a.cg->scale[k] / a.cg->scale_old[k]);
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nch;
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) rescale_kernel(BlasArgs a, const dou
             V::round(lo);   // the stored values define rr
 #pragma unroll
             for (int c = 0; c < N; ++c) val[0] = fma(lo[c].x, lo[c].x, fma(lo[c].y, lo[c].y, val[0]));
-            if (reset_p) {
+            if (reset) {
                 V::store(p_lo, off + i, lo);
             } else {
                 RC pv[N];
@@ -302,9 +307,12 @@ __global__ void __launch_bounds__(kThreads) rescale_kernel(BlasArgs a, const dou
     const bool mx[1] = {false};
     if (block_reduce_arrive<R, 1>(a.red, val, a.n, mx, s_vals)) {
         const int t = threadIdx.x;
-        if (t < a.n && a.cg->active[t]) {
-            a.cg->rr[t] = s_vals[t];
-            a.cg->rr_rel[t] = s_vals[t];
+        if (t < a.n) {
+            if (a.cg->active[t]) {
+                a.cg->rr[t] = s_vals[t];
+                a.cg->rr_rel[t] = s_vals[t];
+            }
+            a.cg->frozen[t] = 0;
         }
     }
 }
@@ -320,7 +328,7 @@ __global__ void __launch_bounds__(kThreads) dot_alpha_kernel(BlasArgs a, const v
     const long long nch = a.len / N;
     const long long off = (long long)k * nch;
     R val[1] = {(R)0};
-    if (a.cg->active[k]) {
+    if (moving(a.cg, k)) {
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nch;
              i += (long long)gridDim.x * blockDim.x) {
             RC pv[N], av[N];
@@ -352,6 +360,28 @@ __global__ void __launch_bounds__(kThreads) residual_norm_kernel(BlasArgs a, con
     const bool mx[2] = {false, true};
     if (block_reduce_arrive<double, 2>(a.red, val, a.n, mx, s_vals))
         finish_reliable(a.cg, s_vals, a.n, tol2);
+}
+
+// [h][V_h][3] <-> [h][3][V_h] per rhs (FP64 complex)
+__global__ void transpose_spinor_kernel(const double2* __restrict__ in, double2* __restrict__ out,
+                                        int halves, int vh, int to_soa) {
+    const int k = blockIdx.y;
+    const long long per = (long long)halves * vh;
+    const double2* src = in + (size_t)k * per * 3;
+    double2* dst = out + (size_t)k * per * 3;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long hb = i / vh, h = i - hb * vh;
+        const size_t base = (size_t)hb * vh * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t aos = base + 3 * (size_t)h + c, soa = base + (size_t)c * vh + h;
+            if (to_soa)
+                dst[soa] = src[aos];
+            else
+                dst[aos] = src[soa];
+        }
+    }
 }
 
 dim3 blas_grid(long long chunks, int n) {
@@ -409,6 +439,13 @@ cudaError_t launch_dot_alpha(const BlasArgs& a, int prec, const void* p, const v
 
 cudaError_t launch_residual_norm(const BlasArgs& a, const double2* r_hi, double tol2, cudaStream_t s) {
     residual_norm_kernel<<<blas_grid(a.len, a.n), kThreads, 0, s>>>(a, r_hi, tol2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_spinor(const double2* in, double2* out, int n, int halves, int vh,
+                                    int to_soa, cudaStream_t s) {
+    transpose_spinor_kernel<<<blas_grid((long long)halves * vh, n), kThreads, 0, s>>>(in, out, halves, vh,
+                                                                                     to_soa);
     return cudaGetLastError();
 }
 

@@ -82,19 +82,19 @@ __device__ __forceinline__ void load_link(Link<RC>& m, const LC* __restrict__ ba
     constexpr int NC = (RECON == 18) ? 9 : (RECON == 14 ? 7 : 6);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        const auto v = ld_c(base + (size_t)c * vh + idx);
+        const auto v = ld_stream(base + (size_t)c * vh + idx);
         m.e[c].x = (R)v.x;
         m.e[c].y = (R)v.y;
     }
     if (RECON == 18) {
 #pragma unroll
         for (int c = 6; c < 9; ++c) {
-            const auto v = ld_c(base + (size_t)c * vh + idx);
+            const auto v = ld_stream(base + (size_t)c * vh + idx);
             m.e[c].x = (R)v.x;
             m.e[c].y = (R)v.y;
         }
     } else if (RECON == 14) {
-        const auto zv = ld_c(base + (size_t)(NC - 1) * vh + idx);
+        const auto zv = ld_stream(base + (size_t)(NC - 1) * vh + idx);
         RC z;
         z.x = (R)zv.x;
         z.y = (R)zv.y;
@@ -117,13 +117,19 @@ __device__ __forceinline__ void scale_link(Link<RC>& m, const R f) {
     }
 }
 
-template <typename SC, typename RC>
-__device__ __forceinline__ void load_spinor(RC (&v)[3], const void* p, int idx) {
+// Spinor element (site idx, colour c) of one rhs: AoS [V_h][3] or SoA [3][V_h].
+template <int LAYOUT>
+__device__ __forceinline__ size_t spinor_index(int idx, int c, int vh) {
+    return LAYOUT == HISQ_SOA ? (size_t)c * vh + idx : 3 * (size_t)idx + c;
+}
+
+template <typename SC, int LAYOUT, typename RC>
+__device__ __forceinline__ void load_spinor(RC (&v)[3], const void* p, int idx, int vh) {
     using R = decltype(RC{}.x);
-    const SC* s = reinterpret_cast<const SC*>(p) + 3 * (size_t)idx;
+    const SC* s = reinterpret_cast<const SC*>(p);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const auto t = ld_c(s + c);
+        const auto t = ld_c(s + spinor_index<LAYOUT>(idx, c, vh));
         v[c].x = (R)t.x;
         v[c].y = (R)t.y;
     }
@@ -152,8 +158,8 @@ __device__ __forceinline__ int wrap(int c, int L) {
     return (c < 0) ? c + L : c;
 }
 
-template <typename S, typename LS, int RU, int RN, int RPT, int EPI>
-__global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs a) {
+template <typename S, typename LS, int RU, int RN, int RPT, int MINB, int EPI, int LAYOUT>
+__global__ void __launch_bounds__(256, MINB) dslash_kernel(const DslashArgs a) {
     using R = typename Traits<S>::R;
     using RC = typename Cx<R>::T;
     using SC = typename Traits<S>::C;
@@ -198,6 +204,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs a) {
 
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
+            if (mu < 3 && a.t_only) continue;
             const int coord = (mu == 0) ? x : (mu == 1) ? y : (mu == 2) ? z : t;
             const int ext = g.L[mu];
             const int stride = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs a) {
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) {
                     RC v[3];
-                    load_spinor<SC, RC>(v, a.in[k0 + j], hn);
+                    load_spinor<SC, LAYOUT, RC>(v, a.in[k0 + j], hn, vh);
                     if (hop == 0 || hop == 2)
                         mv_add(acc[j], m, v);
                     else
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs a) {
                 for (int c = 0; c < 3; ++c) w[c] = acc[j][c];
             } else {
                 RC xv[3];
-                load_spinor<SC, RC>(xv, a.x[k], h);
+                load_spinor<SC, LAYOUT, RC>(xv, a.x[k], h, vh);
                 const R cx = (R)a.cx, cd = (R)a.cd;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -264,7 +271,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs a) {
                 }
                 if (EPI == EPI_XY) {
                     RC yv[3];
-                    load_spinor<SC, RC>(yv, a.y[k], h);
+                    load_spinor<SC, LAYOUT, RC>(yv, a.y[k], h, vh);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         w[c].x += yv[c].x;
@@ -279,14 +286,14 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs a) {
                     }
                 }
             }
-            SC* o = reinterpret_cast<SC*>(a.out[k]) + 3 * (size_t)h;
+            SC* o = reinterpret_cast<SC*>(a.out[k]);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) st_c(o + c, w[c]);
+            for (int c = 0; c < 3; ++c) st_c(o + spinor_index<LAYOUT>(h, c, vh), w[c]);
             if (a.red_mode == RED_NORM_MAX_W) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     // reduce what was stored, so the norm matches the stored vector
-                    const RC sv = stored_value(w[c], o);
+                    const RC sv = stored_value(w[c], (const SC*)o);
                     const R n2 = sv.x * sv.x + sv.y * sv.y;
                     red0[j] += n2;
                     red1[j] = fmax(red1[j], sqrt(n2));
@@ -336,19 +343,22 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs a) {
 // ---------------------------------------------------------------------------
 // Host-side launcher for one instance
 // ---------------------------------------------------------------------------
-template <typename S, typename LS, int RU, int RN, int RPT, int EPI>
+template <typename S, typename LS, int RU, int RN, int RPT, int MINB, int EPI, int LAYOUT>
 cudaError_t launch_dslash_instance(const DslashArgs& a, cudaStream_t s) {
     const int G = a.nrhs / RPT;
-    if (G < 1 || G * RPT != a.nrhs || G > kMaxRhs) return cudaErrorInvalidValue;
+    if (G < 1 || G * RPT != a.nrhs || G > 8) return cudaErrorInvalidValue;
     int bx = 256 / G;
-    if (bx < 32) bx = 32;
     bx &= ~31;
     const dim3 block(bx, G);
-    static int occ_cache[kMaxRhs + 1] = {0};
+    auto* kern = dslash_kernel<S, LS, RU, RN, RPT, MINB, EPI, LAYOUT>;
+    static int occ_cache[9] = {0};
     int occ = occ_cache[G];
     if (occ == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, dslash_kernel<S, LS, RU, RN, RPT, EPI>, bx * G, 0);
+        // the kernel uses almost no shared memory: give the SM's SRAM to L1,
+        // which catches the neighbour gathers
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bx * G, 0);
         if (e != cudaSuccess) return e;
         if (occ < 1) occ = 1;
         occ_cache[G] = occ;
@@ -357,7 +367,7 @@ cudaError_t launch_dslash_instance(const DslashArgs& a, cudaStream_t s) {
     long long cap = (long long)occ * device_sm_count();
     if (nblk > cap) nblk = cap;
     if (nblk > kMaxRedBlocks) nblk = kMaxRedBlocks;
-    dslash_kernel<S, LS, RU, RN, RPT, EPI><<<(unsigned)nblk, block, 0, s>>>(a);
+    kern<<<(unsigned)nblk, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

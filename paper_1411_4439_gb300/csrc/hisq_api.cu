@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -159,9 +160,13 @@ struct hisq_gauge_s {
     double2* U64 = nullptr;      // FP64 R18 copy
     double2* N64 = nullptr;
     size_t link_bytes = 0;
-    int rpt_override = 0;
+    int tune_rpt = 0;            // 0 = automatic
+    int tune_minb = 0;
     void* mdagm_tmp = nullptr;
     size_t mdagm_tmp_bytes = 0;
+    double* dot_partials = nullptr;     // reduction scratch of hisq_cdot
+    unsigned int* dot_counter = nullptr;
+    double* dot_out = nullptr;
     std::vector<Workspace*> ws;
     std::mutex mtx;
 };
@@ -208,6 +213,9 @@ void destroy_gauge(hisq_gauge g) {
     if (g->U64) cudaFree(g->U64);
     if (g->N64) cudaFree(g->N64);
     if (g->mdagm_tmp) cudaFree(g->mdagm_tmp);
+    if (g->dot_partials) cudaFree(g->dot_partials);
+    if (g->dot_counter) cudaFree(g->dot_counter);
+    if (g->dot_out) cudaFree(g->dot_out);
     delete g;
 }
 
@@ -312,11 +320,13 @@ extern "C" hisq_status hisq_gauge_info(hisq_gauge g, int L[4], hisq_prec* prec, 
     return HISQ_OK;
 }
 
-extern "C" hisq_status hisq_set_dslash_rpt(hisq_gauge g, int rpt) {
+extern "C" hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rpt, int minb) {
     if (!g) return fail(HISQ_EINVAL, "NULL handle");
     if (rpt != 0 && rpt != 1 && rpt != 2 && rpt != 4 && rpt != 8)
         return fail(HISQ_EINVAL, "rhs per thread must be 0 (auto), 1, 2, 4 or 8");
-    g->rpt_override = rpt;
+    if (minb < 0 || minb > 8) return fail(HISQ_EINVAL, "min blocks per SM must be 0 (auto) .. 8");
+    g->tune_rpt = rpt;
+    g->tune_minb = minb;
     return HISQ_OK;
 }
 
@@ -396,10 +406,18 @@ int auto_rpt(int n, int prec) {
     return r;
 }
 
-int pick_rpt(hisq_gauge g, int n, int prec, int requested) {
-    int r = requested ? requested : g->rpt_override;
+// Thread mapping for n rhs: the requested rpt, else the handle's setting,
+// else the largest power of two dividing n (at most 8 rhs groups per block).
+DslashTune pick_tune(hisq_gauge g, int n, int prec, int requested, int layout) {
+    DslashTune t;
+    t.layout = layout;
+    int r = requested ? requested : g->tune_rpt;
     if (r == 0 || r > dslash_max_rpt(prec) || n % r != 0 || n / r > 8) r = auto_rpt(n, prec);
-    return r;
+    t.rpt = r;
+    int b = requested ? 0 : g->tune_minb;
+    if (b == 0 || !dslash_mapping_built(prec, r, b)) b = dslash_default_minb(prec, r);
+    t.minb = b;
+    return t;
 }
 
 bool aligned_for(const void* p, int prec) {
@@ -453,10 +471,12 @@ hisq_status check_spinors(hisq_gauge g, const void* const v[], void* const w[], 
 }  // namespace
 
 extern "C" hisq_status hisq_dslash_ex(hisq_gauge g, double mu, const void* const v[], void* const w[],
-                                      int n, int parity, hisq_prec spinor_prec, void* stream) {
+                                      int n, int parity, hisq_prec spinor_prec, hisq_layout layout,
+                                      void* stream) {
     hisq_status st = check_spinors(g, v, w, n, spinor_prec);
     if (st != HISQ_OK) return st;
     if (parity != 0 && parity != 1) return fail(HISQ_EINVAL, "parity must be 0 or 1");
+    if (layout != HISQ_AOS && layout != HISQ_SOA) return fail(HISQ_EINVAL, "unknown layout %d", layout);
     if (!std::isfinite(mu)) return fail(HISQ_EINVAL, "mu must be finite");
     DslashArgs a;
     fill_common(a, g, spinor_prec, parity, n);
@@ -465,15 +485,15 @@ extern "C" hisq_status hisq_dslash_ex(hisq_gauge g, double mu, const void* const
         a.in[k] = v[k];
         a.out[k] = w[k];
     }
-    const int rpt = pick_rpt(g, n, spinor_prec, 0);
+    const DslashTune t = pick_tune(g, n, spinor_prec, 0, layout);
     HISQ_CUDA(launch_dslash(a, spinor_prec, link_recon_u(g, spinor_prec), link_recon_n(g, spinor_prec),
-                            EPI_NONE, rpt, (cudaStream_t)stream));
+                            EPI_NONE, t, (cudaStream_t)stream));
     return HISQ_OK;
 }
 
 extern "C" hisq_status hisq_dslash(hisq_gauge g, const void* const v[], void* const w[], int n,
                                    int parity, hisq_prec spinor_prec, void* stream) {
-    return hisq_dslash_ex(g, 0.0, v, w, n, parity, spinor_prec, stream);
+    return hisq_dslash_ex(g, 0.0, v, w, n, parity, spinor_prec, HISQ_AOS, stream);
 }
 
 extern "C" hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v[], void* const w[],
@@ -491,7 +511,7 @@ extern "C" hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v
         g->mdagm_tmp_bytes = per * kMaxRhs;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const int rpt = pick_rpt(g, n, spinor_prec, 0);
+    const DslashTune t = pick_tune(g, n, spinor_prec, 0, HISQ_AOS);
     const int ru = link_recon_u(g, spinor_prec), rn = link_recon_n(g, spinor_prec);
     DslashArgs a;
     fill_common(a, g, spinor_prec, 1, n);
@@ -499,7 +519,7 @@ extern "C" hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v
         a.in[k] = v[k];
         a.out[k] = (char*)g->mdagm_tmp + per * k;
     }
-    HISQ_CUDA(launch_dslash(a, spinor_prec, ru, rn, EPI_NONE, rpt, s));
+    HISQ_CUDA(launch_dslash(a, spinor_prec, ru, rn, EPI_NONE, t, s));
     DslashArgs b;
     fill_common(b, g, spinor_prec, 0, n);
     b.cx = 4.0 * mass * mass;
@@ -509,7 +529,114 @@ extern "C" hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v
         b.out[k] = w[k];
         b.x[k] = v[k];
     }
-    HISQ_CUDA(launch_dslash(b, spinor_prec, ru, rn, EPI_X, rpt, s));
+    HISQ_CUDA(launch_dslash(b, spinor_prec, ru, rn, EPI_X, t, s));
+    return HISQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Full-lattice fermion matrix, its mu derivative, link force, dot products
+// ---------------------------------------------------------------------------
+extern "C" hisq_status hisq_apply_m(hisq_gauge g, double mass, double mu, int op,
+                                   const void* const v[], void* const w[], int n,
+                                   hisq_prec spinor_prec, void* stream) {
+    hisq_status st = check_spinors(g, v, w, n, spinor_prec);
+    if (st != HISQ_OK) return st;
+    if (op != HISQ_OP_M && op != HISQ_OP_MDAG && op != HISQ_OP_DM_DMU)
+        return fail(HISQ_EINVAL, "unknown operator %d", op);
+    if (!std::isfinite(mass) || !std::isfinite(mu)) return fail(HISQ_EINVAL, "mass and mu must be finite");
+    const size_t half = (size_t)g->g.vh * 3 * prec_complex_bytes(spinor_prec);
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j) {
+            const char* a = (const char*)v[k];
+            const char* b = (const char*)w[j];
+            if (a < b + 2 * half && b < a + 2 * half)
+                return fail(HISQ_EINVAL, "output %d overlaps input %d", j, k);
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    const DslashTune t = pick_tune(g, n, spinor_prec, 0, HISQ_AOS);
+    const int ru = link_recon_u(g, spinor_prec), rn = link_recon_n(g, spinor_prec);
+    for (int par = 0; par < 2; ++par) {
+        DslashArgs a;
+        fill_common(a, g, spinor_prec, par, n);
+        for (int k = 0; k < n; ++k) {
+            a.in[k] = (const char*)v[k] + (1 - par) * half;
+            a.out[k] = (char*)w[k] + par * half;
+            a.x[k] = (const char*)v[k] + par * half;
+        }
+        int epi = EPI_X;
+        if (op == HISQ_OP_M) {
+            set_mu(a, mu);
+            a.cx = 2.0 * mass;
+            a.cd = 1.0;
+        } else if (op == HISQ_OP_MDAG) {
+            set_mu(a, -mu);
+            a.cx = 2.0 * mass;
+            a.cd = -1.0;
+        } else {
+            // d/dmu of the temporal hops: +e^{mu} U v(x+t), +e^{-mu} U^dag v(x-t),
+            // +3 e^{3mu} N v(x+3t), +3 e^{-3mu} N^dag v(x-3t); the kernel subtracts
+            // the backward terms, so their factors carry a minus sign
+            a.ft1 = std::exp(mu);
+            a.bt1 = -std::exp(-mu);
+            a.ft3 = 3.0 * std::exp(3.0 * mu);
+            a.bt3 = -3.0 * std::exp(-3.0 * mu);
+            a.has_mu = 1;
+            a.t_only = 1;
+            epi = EPI_NONE;
+        }
+        HISQ_CUDA(launch_dslash(a, spinor_prec, ru, rn, epi, t, s));
+    }
+    return HISQ_OK;
+}
+
+extern "C" hisq_status hisq_link_force(hisq_gauge g, double mu, int hop, const void* const a[],
+                                      const void* const b[], int n, double coef, void* out,
+                                      void* stream) {
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
+    if (hop != 1 && hop != 3) return fail(HISQ_EINVAL, "hop must be 1 (fat) or 3 (Naik)");
+    if (!a || !b || !out) return fail(HISQ_EINVAL, "NULL pointer");
+    ForcePtrs fp;
+    memset(&fp, 0, sizeof(fp));
+    for (int k = 0; k < n; ++k) {
+        if (!a[k] || !b[k]) return fail(HISQ_EINVAL, "NULL vector pointer for rhs %d", k);
+        if (!aligned_for(a[k], HISQ_F64) || !aligned_for(b[k], HISQ_F64))
+            return fail(HISQ_EINVAL, "vector pointer for rhs %d is not 16-byte aligned", k);
+        fp.a[k] = (const double2*)a[k];
+        fp.b[k] = (const double2*)b[k];
+    }
+    if (!aligned_for(out, HISQ_F64)) return fail(HISQ_EINVAL, "force output is not 16-byte aligned");
+    HISQ_CUDA(launch_link_force(g->g, hop, mu, coef, n, fp, (double2*)out, (cudaStream_t)stream));
+    return HISQ_OK;
+}
+
+extern "C" hisq_status hisq_cdot(hisq_gauge g, const void* const a[], const void* const b[], int n,
+                                long long len, double* out, void* stream) {
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
+    if (len < 1) return fail(HISQ_EINVAL, "len must be >= 1");
+    if (!a || !b || !out) return fail(HISQ_EINVAL, "NULL pointer");
+    ForcePtrs fp;
+    memset(&fp, 0, sizeof(fp));
+    for (int k = 0; k < n; ++k) {
+        if (!a[k] || !b[k]) return fail(HISQ_EINVAL, "NULL vector pointer for rhs %d", k);
+        if (!aligned_for(a[k], HISQ_F64) || !aligned_for(b[k], HISQ_F64))
+            return fail(HISQ_EINVAL, "vector pointer for rhs %d is not 16-byte aligned", k);
+        fp.a[k] = (const double2*)a[k];
+        fp.b[k] = (const double2*)b[k];
+    }
+    std::lock_guard<std::mutex> lock(g->mtx);
+    if (!g->dot_partials) {
+        HISQ_CUDA(cudaMalloc(&g->dot_partials, sizeof(double) * kMaxRedVals * kMaxRedBlocks));
+        HISQ_CUDA(cudaMalloc(&g->dot_counter, sizeof(unsigned int)));
+        HISQ_CUDA(cudaMemset(g->dot_counter, 0, sizeof(unsigned int)));
+        HISQ_CUDA(cudaMalloc(&g->dot_out, sizeof(double) * kMaxRedVals));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    RedScratch red{g->dot_partials, g->dot_counter};
+    HISQ_CUDA(launch_cdot(fp, len, n, red, g->dot_out, s));
+    HISQ_CUDA(cudaMemcpyAsync(out, g->dot_out, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, s));
+    HISQ_CUDA(cudaStreamSynchronize(s));
     return HISQ_OK;
 }
 
@@ -527,6 +654,7 @@ extern "C" void hisq_cg_default_params(hisq_cg_params* p) {
     p->check_every = 10;
     p->use_graphs = 1;
     p->rhs_per_thread = 0;
+    p->spinor_layout = HISQ_SOA;
 }
 
 namespace {
@@ -567,6 +695,13 @@ hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** o
     al((void**)&w->partials, sizeof(double) * kMaxRedVals * kMaxRedBlocks);
     al((void**)&w->counter, sizeof(unsigned int) * 4);
     if (e == cudaSuccess) e = cudaMemset(w->counter, 0, sizeof(unsigned int) * 4);
+    // vectors of rhs that never iterate must still hold finite numbers
+    void* zero_lo[] = {w->r_lo, w->p_lo, w->Ap_lo, w->x_lo, w->t_lo};
+    for (void* z : zero_lo)
+        if (e == cudaSuccess) e = cudaMemset(z, 0, lo);
+    double2* zero_hi[] = {w->b_hi, w->x_hi, w->r_hi, w->t_hi};
+    for (double2* z : zero_hi)
+        if (e == cudaSuccess) e = cudaMemset(z, 0, hi);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&w->cg_host, sizeof(CgScalars));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -582,7 +717,8 @@ hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** o
 struct Solver {
     hisq_gauge g;
     Workspace* w;
-    int n, prec, rpt, full;
+    int n, prec, full;
+    DslashTune tune, tune64;   // inner (low precision) and FP64 Dslash mappings
     double mass, mu;
     double tol2;
 
@@ -593,6 +729,13 @@ struct Solver {
         b.red.partials = w->partials;
         b.red.counter = w->counter;
         b.cg = w->cg;
+        // freeze an rhs when its low-precision residual fell far enough to
+        // risk underflow / stagnation before the host schedules an update
+        b.freeze2 = prec == HISQ_F16 ? 1e-6 : prec == HISQ_F32 ? 1e-10 : 0.0;
+        // A >= 4m^2 for the even-odd operator and for M^dag M at mu = 0, and
+        // alpha = rr / pAp <= rr / (4m^2 |p|^2) <= 1 / (4m^2); twice that
+        // bound leaves room for rounding. No bound is used at mu != 0.
+        b.alpha_max = (mu == 0.0 && mass != 0.0) ? 2.0 / (4.0 * mass * mass) : HUGE_VAL;
         return b;
     }
 
@@ -623,7 +766,7 @@ struct Solver {
                 a.in[k] = lo_ptr(w->p_lo, k);
                 a.out[k] = lo_ptr(w->t_lo, k);
             }
-            e = launch_dslash(a, prec, ru, rn, EPI_NONE, rpt, s);
+            e = launch_dslash(a, prec, ru, rn, EPI_NONE, tune, s);
             if (e != cudaSuccess) return e;
             DslashArgs b = args(0, prec);   // Ap = 4m^2 p - D_eo t, pAp = Re<p, Ap>
             b.cx = 4.0 * mass * mass;
@@ -635,7 +778,7 @@ struct Solver {
                 b.out[k] = lo_ptr(w->Ap_lo, k);
                 b.x[k] = lo_ptr(w->p_lo, k);
             }
-            return launch_dslash(b, prec, ru, rn, EPI_X, rpt, s);
+            return launch_dslash(b, prec, ru, rn, EPI_X, tune, s);
         }
         // full lattice: y = M(mu) p into t, Ap = M(mu)^dag y, then alpha from Re<p, Ap>
         const long long hl = w->len_half;
@@ -649,7 +792,7 @@ struct Solver {
                 a.out[k] = lo_ptr(w->t_lo, k, par * hl);
                 a.x[k] = lo_ptr(w->p_lo, k, par * hl);
             }
-            e = launch_dslash(a, prec, ru, rn, EPI_X, rpt, s);
+            e = launch_dslash(a, prec, ru, rn, EPI_X, tune, s);
             if (e != cudaSuccess) return e;
         }
         for (int par = 0; par < 2; ++par) {
@@ -662,7 +805,7 @@ struct Solver {
                 a.out[k] = lo_ptr(w->Ap_lo, k, par * hl);
                 a.x[k] = lo_ptr(w->t_lo, k, par * hl);
             }
-            e = launch_dslash(a, prec, ru, rn, EPI_X, rpt, s);
+            e = launch_dslash(a, prec, ru, rn, EPI_X, tune, s);
             if (e != cudaSuccess) return e;
         }
         return launch_dot_alpha(blas(), prec, w->p_lo, w->Ap_lo, s);
@@ -679,10 +822,6 @@ struct Solver {
     // r_hi = b - A x_hi in FP64 with the reliable finish (convergence, scale).
     cudaError_t true_residual(cudaStream_t s) const {
         const int f = HISQ_F64;
-        const int r4 = dslash_max_rpt(f);
-        int r64 = 1;
-        while (r64 * 2 <= r4 && n % (r64 * 2) == 0) r64 *= 2;
-        while (n / r64 > 8) r64 *= 2;
         cudaError_t e;
         if (!full) {
             DslashArgs a = args(1, f);   // t = D_oe x
@@ -690,7 +829,7 @@ struct Solver {
                 a.in[k] = hi_ptr(w->x_hi, k);
                 a.out[k] = hi_ptr(w->t_hi, k);
             }
-            e = launch_dslash(a, f, 18, 18, EPI_NONE, r64, s);
+            e = launch_dslash(a, f, 18, 18, EPI_NONE, tune64, s);
             if (e != cudaSuccess) return e;
             DslashArgs b = args(0, f);   // r = b - 4m^2 x + D_eo t
             b.cx = -4.0 * mass * mass;
@@ -703,7 +842,7 @@ struct Solver {
                 b.x[k] = hi_ptr(w->x_hi, k);
                 b.y[k] = hi_ptr(w->b_hi, k);
             }
-            return launch_dslash(b, f, 18, 18, EPI_XY, r64, s);
+            return launch_dslash(b, f, 18, 18, EPI_XY, tune64, s);
         }
         const long long hl = w->len_half;
         for (int par = 0; par < 2; ++par) {   // y = M(mu) x
@@ -716,7 +855,7 @@ struct Solver {
                 a.out[k] = hi_ptr(w->t_hi, k, par * hl);
                 a.x[k] = hi_ptr(w->x_hi, k, par * hl);
             }
-            e = launch_dslash(a, f, 18, 18, EPI_X, r64, s);
+            e = launch_dslash(a, f, 18, 18, EPI_X, tune64, s);
             if (e != cudaSuccess) return e;
         }
         for (int par = 0; par < 2; ++par) {   // r = b - 2m y + D(-mu) y
@@ -730,7 +869,7 @@ struct Solver {
                 a.x[k] = hi_ptr(w->t_hi, k, par * hl);
                 a.y[k] = hi_ptr(w->b_hi, k, par * hl);
             }
-            e = launch_dslash(a, f, 18, 18, EPI_XY, r64, s);
+            e = launch_dslash(a, f, 18, 18, EPI_XY, tune64, s);
             if (e != cudaSuccess) return e;
         }
         return launch_residual_norm(blas(), w->r_hi, tol2, s);
@@ -755,7 +894,7 @@ struct Solver {
             for (int i = 0; i < chunk; ++i) HISQ_CUDA(iterate(s));
             return HISQ_OK;
         }
-        GraphKey key{chunk, mass, mu, rpt};
+        GraphKey key{chunk, mass, mu, tune.rpt * 100 + tune.minb * 10 + tune.layout};
         auto it = w->graphs.find(key);
         if (it == w->graphs.end()) {
             if (w->graphs.size() >= 8) {
@@ -805,6 +944,8 @@ extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const
     if (prm.maxiter < 1) return fail(HISQ_EINVAL, "maxiter must be >= 1");
     if (prm.check_every < 1) prm.check_every = 1;
     if (prm.reliable_every < 1) prm.reliable_every = 1 << 30;
+    if (prm.spinor_layout != HISQ_AOS && prm.spinor_layout != HISQ_SOA)
+        return fail(HISQ_EINVAL, "unknown spinor layout %d", prm.spinor_layout);
     if (!(prm.reliable_delta >= 0.0 && prm.reliable_delta < 1.0))
         return fail(HISQ_EINVAL, "reliable_delta must be in [0, 1)");
 
@@ -821,18 +962,26 @@ extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const
     sv.n = n;
     sv.prec = prm.inner_prec;
     sv.full = full;
-    sv.rpt = pick_rpt(g, n, sv.prec, prm.rhs_per_thread);
+    sv.tune = pick_tune(g, n, sv.prec, prm.rhs_per_thread, prm.spinor_layout);
+    sv.tune64 = pick_tune(g, n, HISQ_F64, 0, prm.spinor_layout);
     sv.mass = mass;
     sv.mu = mu;
     sv.tol2 = tol * tol;
 
     // sources and initial guess into the FP64 blocks
     const size_t vec_bytes = (size_t)w->len * sizeof(double2);
+    const bool soa = prm.spinor_layout == HISQ_SOA;
+    const int halves = full ? 2 : 1;
+    // the caller's vectors are AoS; an SoA solve transposes them through r_hi
+    double2* bdst = soa ? w->r_hi : w->b_hi;
     for (int k = 0; k < n; ++k)
-        HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(w->b_hi, k), b[k], vec_bytes, cudaMemcpyDefault, s));
+        HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(bdst, k), b[k], vec_bytes, cudaMemcpyDefault, s));
+    if (soa) HISQ_CUDA(launch_transpose_spinor(w->r_hi, w->b_hi, n, halves, g->g.vh, 1, s));
     if (prm.use_x0) {
+        double2* xdst = soa ? w->r_hi : w->x_hi;
         for (int k = 0; k < n; ++k)
-            HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(w->x_hi, k), x[k], vec_bytes, cudaMemcpyDefault, s));
+            HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(xdst, k), x[k], vec_bytes, cudaMemcpyDefault, s));
+        if (soa) HISQ_CUDA(launch_transpose_spinor(w->r_hi, w->x_hi, n, halves, g->g.vh, 1, s));
     } else {
         HISQ_CUDA(cudaMemsetAsync(w->x_hi, 0, vec_bytes * n, s));
     }
@@ -847,8 +996,13 @@ extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const
     HISQ_CUDA(launch_reliable_rescale(sv.blas(), sv.prec, w->r_hi, w->r_lo, w->p_lo, 1, s));
     HISQ_CUDA(sv.poll(s));
 
-    int iters_k[kMaxRhs];
-    for (int k = 0; k < n; ++k) iters_k[k] = 0;
+    // HISQ_DEBUG_CG=1 prints the device CG scalars at every host poll (stderr)
+    static const bool debug = [] {
+        const char* e = getenv("HISQ_DEBUG_CG");
+        return e != nullptr && e[0] != '\0' && e[0] != '0';
+    }();
+    int iters_k[kMaxRhs], seen_restarts[kMaxRhs], bad_updates[kMaxRhs];
+    for (int k = 0; k < n; ++k) iters_k[k] = seen_restarts[k] = bad_updates[k] = 0;
     int iter = 0, since_rel = 0, reliable = 0;
     hisq_status result = HISQ_OK;
     const double d2 = prm.reliable_delta * prm.reliable_delta;
@@ -873,22 +1027,47 @@ extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const
         since_rel += chunk;
         HISQ_CUDA(sv.poll(s));
         const CgScalars& h = *w->cg_host;
+        if (debug) {
+            fprintf(stderr, "[hisq cg] iter %d flags %d\n", iter, h.flags);
+            for (int k = 0; k < n; ++k)
+                fprintf(stderr, "  rhs %d active %d frozen %d restarts %d rr %.3e rr_rel %.3e pAp %.3e alpha %.3e "
+                        "beta %.3e rr_true %.3e bb %.3e scale %.3e\n", k, h.active[k], h.frozen[k],
+                        h.restarts[k], h.rr[k], h.rr_rel[k], h.pAp[k], h.alpha[k], h.beta[k], h.rr_true[k],
+                        h.bb[k], h.scale[k]);
+        }
         if (h.flags) break;
         bool need = since_rel >= prm.reliable_every || iter >= prm.maxiter;
-        for (int k = 0; k < n && !need; ++k) {
+        bool restarted[kMaxRhs];
+        for (int k = 0; k < n; ++k) {
+            restarted[k] = h.active[k] && h.restarts[k] != seen_restarts[k];
+            seen_restarts[k] = h.restarts[k];
             if (!h.active[k]) continue;
+            if (h.frozen[k] || restarted[k]) need = true;
             if (h.rr[k] <= d2 * h.rr_rel[k]) need = true;
             if (h.rr[k] <= sv.tol2 * h.bb[k] * h.scale[k] * h.scale[k]) need = true;
         }
         if (need) {
             int was[kMaxRhs];
-            for (int k = 0; k < n; ++k) was[k] = h.active[k];
+            double before[kMaxRhs];
+            for (int k = 0; k < n; ++k) {
+                was[k] = h.active[k];
+                before[k] = h.rr_true[k];
+            }
             HISQ_CUDA(sv.reliable_update(s));
             HISQ_CUDA(sv.poll(s));
             ++reliable;
             since_rel = 0;
-            for (int k = 0; k < n; ++k)
-                if (was[k] && !w->cg_host->active[k]) iters_k[k] = iter;
+            const CgScalars& a = *w->cg_host;
+            for (int k = 0; k < n; ++k) {
+                if (was[k] && !a.active[k]) iters_k[k] = iter;
+                // restarts that bring no progress of the FP64 residual are a breakdown
+                if (was[k] && a.active[k] && restarted[k] && !(a.rr_true[k] < before[k]))
+                    ++bad_updates[k];
+                else
+                    bad_updates[k] = 0;
+                if (bad_updates[k] >= 3) result = HISQ_EBREAKDOWN;
+            }
+            if (result == HISQ_EBREAKDOWN) break;
         }
     }
     if (result == HISQ_ENOCONV) {
@@ -903,12 +1082,17 @@ extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const
     const CgScalars& h = *w->cg_host;
     if (h.flags & kFlagNaN)
         result = fail(HISQ_ENAN, "non-finite value in the CG (source or residual)");
-    else if (h.flags & kFlagBreakdown)
-        result = fail(HISQ_EBREAKDOWN, "CG breakdown: <p, A p> <= 0 or not finite");
+    else if ((h.flags & kFlagBreakdown) || result == HISQ_EBREAKDOWN)
+        result = fail(HISQ_EBREAKDOWN, "CG breakdown: <p, A p> <= 0 repeatedly with no FP64 progress");
     else if (result == HISQ_ENOCONV)
         fail(HISQ_ENOCONV, "CG did not converge in %d iterations", prm.maxiter);
+    double2* xsrc = w->x_hi;
+    if (soa) {
+        HISQ_CUDA(launch_transpose_spinor(w->x_hi, w->t_hi, n, halves, g->g.vh, 0, s));
+        xsrc = w->t_hi;
+    }
     for (int k = 0; k < n; ++k)
-        HISQ_CUDA(cudaMemcpyAsync(x[k], sv.hi_ptr(w->x_hi, k), vec_bytes, cudaMemcpyDefault, s));
+        HISQ_CUDA(cudaMemcpyAsync(x[k], sv.hi_ptr(xsrc, k), vec_bytes, cudaMemcpyDefault, s));
     HISQ_CUDA(cudaStreamSynchronize(s));
     if (stats) {
         memset(stats, 0, sizeof(*stats));

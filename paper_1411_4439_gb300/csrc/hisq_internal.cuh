@@ -97,6 +97,11 @@ struct CgScalars {
     double scale[kMaxRhs];     // low-precision vectors hold scale * true vector
     double scale_old[kMaxRhs];
     int active[kMaxRhs];       // 1 while rhs k is iterating
+    int frozen[kMaxRhs];       // 1: residual fell below freeze2 * rr_rel; skip until the next reliable update
+    int stall[kMaxRhs];        // 1: <p,Ap> <= 0 in low precision; this iteration restarts p = r
+    int restarts[kMaxRhs];     // number of such restarts in this solve
+    double freeze2;            // squared residual drop that freezes an rhs (precision safety net)
+    double alpha_max;          // alpha above this bound (1/lambda_min) means lost precision: restart
     int flags;                 // kFlagBreakdown | kFlagNaN
 };
 constexpr int kFlagBreakdown = 1;
@@ -133,6 +138,7 @@ struct DslashArgs {
     double cx, cd;                      // out = [y] + cx * x + cd * (D in)
     double ft1, bt1, ft3, bt3;          // temporal hop factors e^{+mu}, e^{-mu}, e^{3mu}, e^{-3mu}
     int has_mu;                         // 1 if any factor differs from 1
+    int t_only;                         // 1: temporal hops only (d D / d mu)
     double r12_inv_scale;               // 1 / s for R12 fat links
     int red_mode;
     int finish;
@@ -145,14 +151,29 @@ struct DslashArgs {
 // Epilogue kinds (template parameter of the Dslash kernel)
 enum Epi : int { EPI_NONE = 0, EPI_X = 1, EPI_XY = 2 };
 
+// Thread mapping and spinor layout of one launch: rpt rhs per thread,
+// compiled for at least minb resident 256-thread blocks per SM.
+struct DslashTune {
+    int rpt;
+    int minb;
+    int layout;   // HISQ_AOS or HISQ_SOA
+};
+
 // Dispatch into the instantiated kernels. prec is the spinor and link storage
-// precision; rpt = rhs per thread (1, 2, 4, 8; F64: 1, 2, 4); nrhs must be a
-// multiple of rpt with nrhs / rpt <= 8.
-cudaError_t launch_dslash(const DslashArgs& a, int prec, int ru, int rn, int epi, int rpt,
-                          cudaStream_t s);
+// precision; nrhs must be a multiple of t.rpt with nrhs / t.rpt <= 8.
+cudaError_t launch_dslash(const DslashArgs& a, int prec, int ru, int rn, int epi,
+                          const DslashTune& t, cudaStream_t s);
 bool dslash_variant_supported(int prec, int ru, int rn, int epi);
+// Built (rpt, minb) pairs of a precision, and the default minb for an rpt (0 if none).
+bool dslash_mapping_built(int prec, int rpt, int minb);
+int dslash_default_minb(int prec, int rpt);
 // Largest rhs-per-thread value instantiated for a precision.
 int dslash_max_rpt(int prec);
+
+// Spinor layout conversion of FP64 vectors: n rhs, `halves` parity blocks of
+// vh sites each; to_soa: [h][V_h][3] -> [h][3][V_h], else the reverse.
+cudaError_t launch_transpose_spinor(const double2* in, double2* out, int n, int halves, int vh,
+                                    int to_soa, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Link packing (gauge.cu)
@@ -178,6 +199,8 @@ struct BlasArgs {
     long long len;       // complex elements per rhs (vh * 3)
     RedScratch red;
     CgScalars* cg;
+    double freeze2;      // norm_bb stores it into cg->freeze2
+    double alpha_max;    // norm_bb stores it into cg->alpha_max
 };
 // x_lo += alpha p; r -= alpha Ap; rr' = |r|^2 -> beta = rr'/rr, rr = rr'
 cudaError_t launch_cg_update_xr(const BlasArgs& a, int prec, void* x, void* r,
@@ -204,6 +227,21 @@ cudaError_t launch_copy_residual(const BlasArgs& a, const double2* b, double2* r
 // rr = rr_rel = |r_lo|^2 (active rhs only)
 cudaError_t launch_reliable_rescale(const BlasArgs& a, int prec, const double2* r_hi,
                                     void* r_lo, void* p_lo, int reset_p, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Gradients (force.cu)
+// ---------------------------------------------------------------------------
+struct ForcePtrs {
+    const double2* a[kMaxRhs];   // full-lattice parity-blocked FP64 vectors [2][vh][3]
+    const double2* b[kMaxRhs];
+};
+// out[mu][i] += coef * sum_k [f a_k(i) b_k(i+hop mu)^dag - (1/f) b_k(i) a_k(i+hop mu)^dag]
+// with f = e^{hop mu_chem} on temporal links; out canonical complex128 [4][V][3][3].
+cudaError_t launch_link_force(const Geom& g, int hop, double mu_chem, double coef, int n,
+                              const ForcePtrs& ptrs, double2* out, cudaStream_t s);
+// out[2k] + i out[2k+1] = <a_k, b_k> over len complex numbers, FP64, deterministic
+cudaError_t launch_cdot(const ForcePtrs& vw, long long len, int n, RedScratch red, double* out,
+                        cudaStream_t s);
 
 int device_sm_count();
 

@@ -66,15 +66,26 @@ __device__ __forceinline__ void finish_values(const RedScratch& red, int nvals, 
 // Finish logic shared by the Dslash and vector kernels
 // ---------------------------------------------------------------------------
 
-// pAp -> alpha_k = rr_k / pAp_k for active rhs; breakdown if pAp <= 0 or not finite.
+// An rhs moves (takes part in alpha/beta updates) while active and not frozen.
+__device__ __forceinline__ bool moving(const CgScalars* cg, int k) {
+    return cg->active[k] && !cg->frozen[k];
+}
+
+// pAp -> alpha_k = rr_k / pAp_k for moving rhs. A non-finite pAp is an error;
+// pAp <= 0 means the low-precision iteration lost A-conjugacy: alpha = 0 and
+// this iteration restarts the rhs from p = r (beta = 0).
 __device__ __forceinline__ void finish_cg_alpha(CgScalars* cg, const double* vals, int n) {
     const int k = threadIdx.x + threadIdx.y * blockDim.x;
     if (k < n) {
         const double pAp = vals[k];
         double alpha = 0.0;
-        if (cg->active[k]) {
-            if (!(pAp > 0.0) || !isfinite(pAp)) {
-                atomicOr(&cg->flags, kFlagBreakdown);
+        if (moving(cg, k)) {
+            if (!isfinite(pAp)) {
+                atomicOr(&cg->flags, kFlagNaN);
+            } else if (!(pAp > 0.0) || !(cg->rr[k] <= cg->alpha_max * pAp)) {
+                // pAp <= 0, or alpha above 1/lambda_min: the low-precision
+                // iteration lost conjugacy; restart this rhs from p = r
+                cg->stall[k] = 1;
             } else {
                 alpha = cg->rr[k] / pAp;
             }
@@ -84,18 +95,25 @@ __device__ __forceinline__ void finish_cg_alpha(CgScalars* cg, const double* val
     }
 }
 
-// rr' -> beta_k = rr'_k / rr_k, rr_k = rr'_k for active rhs.
+// rr' -> beta_k = rr'_k / rr_k, rr_k = rr'_k for moving rhs; freezes an rhs
+// whose residual fell by more than freeze2 since the last reliable update.
 __device__ __forceinline__ void finish_cg_beta(CgScalars* cg, const double* vals, int n) {
     const int k = threadIdx.x + threadIdx.y * blockDim.x;
     if (k < n) {
         double beta = 0.0;
-        if (cg->active[k]) {
+        if (moving(cg, k)) {
             const double rr_new = vals[k];
             if (!isfinite(rr_new)) {
                 atomicOr(&cg->flags, kFlagNaN);
             } else {
-                beta = rr_new / cg->rr[k];
+                if (cg->stall[k]) {
+                    cg->stall[k] = 0;
+                    cg->restarts[k] += 1;
+                } else if (cg->rr[k] > 0.0) {
+                    beta = rr_new / cg->rr[k];
+                }
                 cg->rr[k] = rr_new;
+                if (rr_new <= cg->freeze2 * cg->rr_rel[k]) cg->frozen[k] = 1;
             }
         }
         cg->beta[k] = beta;

@@ -27,15 +27,19 @@ HISQ_EBREAKDOWN, HISQ_ENAN, HISQ_ECUDA, HISQ_ETIMEOUT, HISQ_ENOMEM = 4, 5, 6, 7,
 # precisions and compressions
 HISQ_F64, HISQ_F32, HISQ_F16 = 0, 1, 2
 HISQ_R18, HISQ_R12, HISQ_R14 = 18, 12, 14
+HISQ_AOS, HISQ_SOA = 0, 1
 
 STATUS_NAMES = {0: "HISQ_OK", 1: "HISQ_EINVAL", 2: "HISQ_ERECON", 3: "HISQ_ENOCONV",
                 4: "HISQ_EBREAKDOWN", 5: "HISQ_ENAN", 6: "HISQ_ECUDA", 7: "HISQ_ETIMEOUT",
                 8: "HISQ_ENOMEM"}
 MAX_RHS = 16
 
+HISQ_OP_M, HISQ_OP_MDAG, HISQ_OP_DM_DMU = 0, 1, 2
+
 EXPORTED = ["hisq_version", "hisq_last_error", "hisq_gauge_load", "hisq_gauge_free",
-            "hisq_gauge_info", "hisq_set_dslash_rpt", "hisq_link_compress",
+            "hisq_gauge_info", "hisq_set_dslash_mapping", "hisq_link_compress",
             "hisq_link_reconstruct", "hisq_dslash", "hisq_dslash_ex", "hisq_mdagm",
+            "hisq_apply_m", "hisq_link_force", "hisq_cdot",
             "hisq_cg_default_params", "hisq_cg_solve"]
 
 
@@ -51,7 +55,7 @@ class hisq_cg_params(ctypes.Structure):
                 ("reliable_delta", ctypes.c_double), ("inner_prec", ctypes.c_int),
                 ("use_x0", ctypes.c_int), ("even_odd", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("rhs_per_thread", ctypes.c_int)]
+                ("rhs_per_thread", ctypes.c_int), ("spinor_layout", ctypes.c_int)]
 
 
 class hisq_cg_stats(ctypes.Structure):
@@ -80,13 +84,19 @@ def library() -> ctypes.CDLL:
                                     ctypes.POINTER(vp)]),
         "hisq_gauge_free": (c_int, [vp]),
         "hisq_gauge_info": (c_int, [vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_size_t)]),
-        "hisq_set_dslash_rpt": (c_int, [vp, c_int]),
+        "hisq_set_dslash_mapping": (c_int, [vp, c_int, c_int]),
         "hisq_link_compress": (c_int, [ip, vp, c_int, vp, ctypes.POINTER(c_double), vp]),
         "hisq_link_reconstruct": (c_int, [ip, vp, c_int, vp, vp]),
         "hisq_dslash": (c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int, c_int, vp]),
         "hisq_dslash_ex": (c_int, [vp, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int,
-                                   c_int, vp]),
+                                   c_int, c_int, vp]),
         "hisq_mdagm": (c_int, [vp, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int, vp]),
+        "hisq_apply_m": (c_int, [vp, c_double, c_double, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                 c_int, c_int, vp]),
+        "hisq_link_force": (c_int, [vp, c_double, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
+                                    c_double, vp, vp]),
+        "hisq_cdot": (c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, ctypes.c_longlong,
+                              ctypes.POINTER(c_double), vp]),
         "hisq_cg_default_params": (None, [ctypes.POINTER(hisq_cg_params)]),
         "hisq_cg_solve": (c_int, [vp, c_double, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
                                   c_double, ctypes.POINTER(hisq_cg_params),
@@ -226,8 +236,9 @@ def hisq_gauge_info(g: Gauge) -> dict:
                 device_bytes=nbytes.value)
 
 
-def hisq_set_dslash_rpt(g: Gauge, rpt: int) -> None:
-    _check(library().hisq_set_dslash_rpt(g.handle, int(rpt)))
+def hisq_set_dslash_mapping(g: Gauge, rhs_per_thread: int, min_blocks: int = 0) -> None:
+    """Dslash rhs per thread and register budget (min blocks per SM); 0 = automatic."""
+    _check(library().hisq_set_dslash_mapping(g.handle, int(rhs_per_thread), int(min_blocks)))
 
 
 def hisq_link_compress(L, links, recon, packed, stream=None) -> float:
@@ -245,14 +256,16 @@ def hisq_link_reconstruct(L, packed, recon, links, stream=None) -> None:
 
 def hisq_dslash(g: Gauge, v, w, parity: int, prec: int, stream=None) -> None:
     """w[k] = D_{p,1-p} v[k] (Eq. 3, Eq. 4); v, w lists of device tensors."""
-    hisq_dslash_ex(g, 0.0, v, w, parity, prec, stream)
+    hisq_dslash_ex(g, 0.0, v, w, parity, prec, HISQ_AOS, stream)
 
 
-def hisq_dslash_ex(g: Gauge, mu: float, v, w, parity: int, prec: int, stream=None) -> None:
+def hisq_dslash_ex(g: Gauge, mu: float, v, w, parity: int, prec: int, layout: int = HISQ_AOS,
+                   stream=None) -> None:
+    """Dslash with a chemical potential on the temporal hops; AoS or SoA spinors."""
     if len(v) != len(w):
         raise ValueError("v and w need the same number of rhs")
     _check(library().hisq_dslash_ex(g.handle, float(mu), _ptr_array(v), _ptr_array(w), len(v),
-                                    int(parity), int(prec), _stream_handle(stream, *v)))
+                                    int(parity), int(prec), int(layout), _stream_handle(stream, *v)))
 
 
 def hisq_mdagm(g: Gauge, mass: float, v, w, prec: int, stream=None) -> None:
@@ -261,6 +274,38 @@ def hisq_mdagm(g: Gauge, mass: float, v, w, prec: int, stream=None) -> None:
         raise ValueError("v and w need the same number of rhs")
     _check(library().hisq_mdagm(g.handle, float(mass), _ptr_array(v), _ptr_array(w), len(v),
                                 int(prec), _stream_handle(stream, *v)))
+
+
+def hisq_apply_m(g: Gauge, mass: float, mu: float, op: int, v, w, prec: int, stream=None) -> None:
+    """w[k] = M(mu) v[k], M(mu)^dag v[k] or dM/dmu v[k] on parity-blocked [2 V_h][3] vectors."""
+    if len(v) != len(w):
+        raise ValueError("v and w need the same number of rhs")
+    _check(library().hisq_apply_m(g.handle, float(mass), float(mu), int(op), _ptr_array(v),
+                                  _ptr_array(w), len(v), int(prec), _stream_handle(stream, *v)))
+
+
+def hisq_link_force(g: Gauge, mu: float, hop: int, a, b, coef: float, out, stream=None) -> None:
+    """out[mu][x] += coef * sum_k [f a_k(x) b_k(x+hop mu)^dag - b_k(x) a_k(x+hop mu)^dag / f]."""
+    if len(a) != len(b):
+        raise ValueError("a and b need the same number of rhs")
+    _check(library().hisq_link_force(g.handle, float(mu), int(hop), _ptr_array(a), _ptr_array(b),
+                                     len(a), float(coef), _ptr(out), _stream_handle(stream, out)))
+
+
+def hisq_cdot(g: Gauge, a, b, stream=None) -> np.ndarray:
+    """<a_k, b_k> for FP64 complex device vectors; returns complex128 array of n values."""
+    if len(a) != len(b):
+        raise ValueError("a and b need the same number of rhs")
+    n = len(a)
+    length = int(a[0].numel()) // (2 if str(a[0].dtype).endswith("float64") else 1)
+    for t in list(a) + list(b):
+        if t.numel() != a[0].numel():
+            raise ValueError("all vectors need the same length")
+    out = (ctypes.c_double * (2 * n))()
+    _check(library().hisq_cdot(g.handle, _ptr_array(a), _ptr_array(b), n, length, out,
+                               _stream_handle(stream, *a)))
+    arr = np.frombuffer(out, dtype=np.float64).copy()
+    return arr[0::2] + 1j * arr[1::2]
 
 
 def hisq_cg_default_params() -> hisq_cg_params:

@@ -97,7 +97,7 @@ def test_every_thread_mapping_gives_the_same_result(gpu_lib, prec, ru, rn, n):
         for rpt in (1, 2, 4, 8):
             if rpt > maxr or n % rpt or n // rpt > 8:
                 continue
-            H.hisq_set_dslash_rpt(g, rpt)
+            H.hisq_set_dslash_mapping(g, rpt)
             wd = [torch.full_like(t, float("nan")) for t in vd]
             H.hisq_dslash(g, vd, wd, 0, prec)
             torch.cuda.synchronize()

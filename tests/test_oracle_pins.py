@@ -348,3 +348,17 @@ def test_site_evaluation_matches_array_form(mu_chem):
     ws = O.dslash_at_sites(U, N, v, sites, mu_chem)
     for s, (x, y, z, t) in enumerate(sites):
         assert np.abs(ws[:, s] - w[:, t, z, y, x]).max() < 1e-13
+
+
+@pytest.mark.parametrize("mu_chem", [0.0, 0.2])
+def test_mu_derivative_is_finite_difference_of_dslash(mu_chem):
+    L = (4, 4, 4, 6)
+    U, N = gen.hisq_links(L, seed=81)
+    v = gaussian_full(L, 2, 82)
+    h = 1e-5
+    fd = (O.dslash(U, N, v, mu_chem + h) - O.dslash(U, N, v, mu_chem - h)) / (2 * h)
+    assert rel(O.apply_dM_dmu(U, N, v, mu_chem), fd) < 1e-9
+    # and d(M^dag)/dmu is the adjoint of dM/dmu
+    w = gaussian_full(L, 2, 83)
+    fd_dag = (O.apply_Mdag(U, N, w, 0.1, mu_chem + h) - O.apply_Mdag(U, N, w, 0.1, mu_chem - h)) / (2 * h)
+    assert abs(np.vdot(v, fd_dag) - np.vdot(O.apply_dM_dmu(U, N, v, mu_chem), w)) < 1e-8 * np.linalg.norm(v) * np.linalg.norm(w)
