@@ -127,10 +127,15 @@ hisq_status hisq_gauge_info(hisq_gauge g, int L[4], hisq_prec* prec,
 /*
  * Tuning of the Dslash thread mapping for this handle: rhs handled per
  * thread (1, 2, 4, 8; FP64: 1, 2, 4) and the minimum resident blocks per SM
- * the kernel is compiled for (register budget). 0 = automatic. Pairs that
- * are not built, or rpt values that do not divide n, fall back to automatic.
+ * the kernel is compiled for (register budget); 0 = automatic. Flags:
+ * HISQ_MAP_PACKED for paired FP32 (f32x2) complex arithmetic,
+ * HISQ_MAP_L2_PREFETCH to bulk-prefetch each tile's links into L2. Mappings
+ * that are not built, or rpt values that do not divide n, fall back to the
+ * automatic choice.
  */
-hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_blocks);
+enum { HISQ_MAP_PACKED = 1, HISQ_MAP_L2_PREFETCH = 2 };
+hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_blocks,
+                                    int flags);
 
 /*
  * Compress a canonical link field to `r` reals per link (R18/R14/R12, same
@@ -190,7 +195,14 @@ hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v[],
  * Eq. 2. v and w: n device pointers each; w must not overlap any v.
  * Asynchronous on `stream`.
  */
-enum { HISQ_OP_M = 0, HISQ_OP_MDAG = 1, HISQ_OP_DM_DMU = 2 };
+enum {
+    HISQ_OP_M = 0,
+    HISQ_OP_MDAG = 1,
+    HISQ_OP_DM_DMU = 2,    /* k-th derivative: HISQ_OP_DM_DMU + k - 1, k = 1..4; */
+    HISQ_OP_D2M_DMU2 = 3,  /* the factors become +e^{mu}, +(-1)^k e^{-mu} on    */
+    HISQ_OP_D3M_DMU3 = 4,  /* the one-hops and 3^k e^{3mu}, (-3)^k e^{-3mu} on  */
+    HISQ_OP_D4M_DMU4 = 5   /* the Naik hops (signs as for the first derivative) */
+};
 hisq_status hisq_apply_m(hisq_gauge g, double mass, double mu, int op,
                          const void* const v[], void* const w[], int n,
                          hisq_prec spinor_prec, void* stream);

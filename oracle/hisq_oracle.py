@@ -193,13 +193,44 @@ def apply_dM_dmu(U, N, v, mu_chem: float = 0.0):
     d/dmu of  e^{mu} U_3(x) v(x+t) - e^{-mu} U_3(x-t)^dag v(x-t)
             + e^{3mu} N_3(x) v(x+3t) - e^{-3mu} N_3(x-3t)^dag v(x-3t).
     """
+    return apply_dnM_dmun(U, N, v, mu_chem, 1)
+
+
+def apply_dnM_dmun(U, N, v, mu_chem: float, order: int):
+    """d^k M / dmu^k v for k = order >= 1 (the mu-derivatives that enter Eq. 1-2).
+
+    Only the temporal terms of Eq. 3 depend on mu; the k-th derivative of
+    e^{+-mu} is (+-1)^k e^{+-mu} and of e^{+-3mu} is (+-3)^k e^{+-3mu}.
+    """
     v = np.asarray(v, dtype=COMPLEX)
+    k = int(order)
     mu = 3
     w = np.exp(mu_chem) * _matvec(U[mu], shift(v, mu, +1, 1))
-    w += np.exp(-mu_chem) * _matvec(_dagger(shift(U[mu], mu, -1, 0)), shift(v, mu, -1, 1))
-    w += 3.0 * np.exp(3.0 * mu_chem) * _matvec(N[mu], shift(v, mu, +3, 1))
-    w += 3.0 * np.exp(-3.0 * mu_chem) * _matvec(_dagger(shift(N[mu], mu, -3, 0)), shift(v, mu, -3, 1))
+    w -= (-1.0) ** k * np.exp(-mu_chem) * _matvec(_dagger(shift(U[mu], mu, -1, 0)), shift(v, mu, -1, 1))
+    w += 3.0 ** k * np.exp(3.0 * mu_chem) * _matvec(N[mu], shift(v, mu, +3, 1))
+    w -= (-3.0) ** k * np.exp(-3.0 * mu_chem) * _matvec(_dagger(shift(N[mu], mu, -3, 0)), shift(v, mu, -3, 1))
     return w
+
+
+def apply_Minv(U, N, v, mass: float, mu_chem: float = 0.0, tol: float = 1e-13):
+    """M(mu)^-1 v = (M^dag M)^-1 M^dag v on the full lattice (CG on the normal equations)."""
+    x, _ = cg(lambda q: apply_MdagM(U, N, q, mass, mu_chem), apply_Mdag(U, N, v, mass, mu_chem), tol)
+    return x
+
+
+def trace_word_bilinear(U, N, eta, mass: float, mu_chem: float, orders, tol: float = 1e-13):
+    """eta_k^dag  d^{n1}M M^-1 d^{n2}M M^-1 ... d^{nj}M M^-1  eta_k, per rhs k (Eq. 2).
+
+    ``orders`` = (n1, ..., nj); each factor d^{n}M M^-1 is applied from the
+    right. The mean over noise vectors with E[eta eta^dag] = 1 estimates the
+    trace of the word.
+    """
+    v = np.asarray(eta, dtype=COMPLEX)
+    for order in reversed(list(orders)):
+        v = apply_Minv(U, N, v, mass, mu_chem, tol)
+        v = apply_dnM_dmun(U, N, v, mu_chem, order)
+    axes = tuple(range(1, v.ndim))
+    return np.sum(np.conj(eta) * v, axis=axes)
 
 
 def apply_Ae(U, N, v_half, L, mass: float):

@@ -110,6 +110,42 @@ __device__ bool block_reduce_arrive(const RedScratch& red, R (&val)[NV], int n, 
     return true;
 }
 
+// The low-precision solution increment x_lo is kept in at least FP32: it
+// collects alpha p over up to a reliable-update cycle, and in FP16 the small
+// increments would round away against its growing value.
+template <typename S> struct XType { using T = S; };
+template <> struct XType<__half> { using T = float; };
+
+// N complex numbers of an FP32 / FP64 vector starting at complex index i * N.
+template <typename SX, int N> struct XVec;
+template <int N> struct XVec<float, N> {
+    static_assert(N % 2 == 0, "FP32 chunks hold pairs of complex numbers");
+    __device__ static void load(const void* b, long long i, float2 (&v)[N]) {
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(b) + i * (N / 2) + c);
+            v[2 * c] = make_float2(t.x, t.y);
+            v[2 * c + 1] = make_float2(t.z, t.w);
+        }
+    }
+    __device__ static void store(void* b, long long i, const float2 (&v)[N]) {
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c)
+            reinterpret_cast<float4*>(b)[i * (N / 2) + c] =
+                make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
+    }
+};
+template <int N> struct XVec<double, N> {
+    __device__ static void load(const void* b, long long i, double2 (&v)[N]) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] = __ldg(reinterpret_cast<const double2*>(b) + i * N + c);
+    }
+    __device__ static void store(void* b, long long i, const double2 (&v)[N]) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) reinterpret_cast<double2*>(b)[i * N + c] = v[c];
+    }
+};
+
 // x += alpha p ; r -= alpha Ap ; rr' = |r|^2 ; finish: beta = rr'/rr
 template <typename S>
 __global__ void __launch_bounds__(kThreads) update_xr_kernel(BlasArgs a, void* x, void* r,
@@ -117,6 +153,7 @@ __global__ void __launch_bounds__(kThreads) update_xr_kernel(BlasArgs a, void* x
     using V = Vec<S>;
     using R = typename V::R;
     using RC = typename CxOf<R>::T;
+    using X = XVec<typename XType<S>::T, V::N>;
     constexpr int N = V::N;
     const int k = blockIdx.y;
     const long long nch = a.len / N;
@@ -127,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) update_xr_kernel(BlasArgs a, void* x
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nch;
              i += (long long)gridDim.x * blockDim.x) {
             RC xv[N], rv[N], pv[N], av[N];
-            V::load(x, off + i, xv);
+            X::load(x, off + i, xv);
             V::load(r, off + i, rv);
             V::load(p, off + i, pv);
             V::load(Ap, off + i, av);
@@ -138,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) update_xr_kernel(BlasArgs a, void* x
                 rv[c].x = fma(-alpha, av[c].x, rv[c].x);
                 rv[c].y = fma(-alpha, av[c].y, rv[c].y);
             }
-            V::store(x, off + i, xv);
+            X::store(x, off + i, xv);
             V::store(r, off + i, rv);
             V::round(rv);   // the norm is that of the stored residual
 #pragma unroll
@@ -182,6 +219,7 @@ __global__ void __launch_bounds__(kThreads) accum_kernel(BlasArgs a, double2* x_
     using V = Vec<S>;
     using R = typename V::R;
     using RC = typename CxOf<R>::T;
+    using X = XVec<typename XType<S>::T, V::N>;
     constexpr int N = V::N;
     const int k = blockIdx.y;
     if (!a.cg->active[k]) return;
@@ -192,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) accum_kernel(BlasArgs a, double2* x_
          i += (long long)gridDim.x * blockDim.x) {
         RC lo[N];
         double2 hi[N];
-        V::load(x_lo, off + i, lo);
+        X::load(x_lo, off + i, lo);
         load64<N>(x_hi, off + i, hi);
 #pragma unroll
         for (int c = 0; c < N; ++c) {
@@ -202,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) accum_kernel(BlasArgs a, double2* x_
             lo[c].y = (R)0;
         }
         store64<N>(x_hi, off + i, hi);
-        V::store(x_lo, off + i, lo);
+        X::store(x_lo, off + i, lo);
     }
 }
 
@@ -272,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) rescale_kernel(BlasArgs a, const dou
     const long long off = (long long)k * nch;
     R val[1] = {(R)0};
     if (a.cg->active[k]) {
-        const bool reset = reset_p != 0;
+        const bool reset = reset_p != 0 || a.cg->reset_p[k] != 0;
         const double sc = a.cg->scale[k];
         const R ratio = (R)(a.cg->scale[k] / a.cg->scale_old[k]);
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nch;
@@ -313,6 +351,7 @@ __global__ void __launch_bounds__(kThreads) rescale_kernel(BlasArgs a, const dou
                 a.cg->rr_rel[t] = s_vals[t];
             }
             a.cg->frozen[t] = 0;
+            a.cg->reset_p[t] = 0;
         }
     }
 }

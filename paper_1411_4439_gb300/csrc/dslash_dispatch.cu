@@ -1,31 +1,51 @@
 // Routes a Dslash request to the kernel family built for its storage
-// precision and link compression (see dslash_inst.cu).
+// precision and link compression (see dslash_inst.cu), and owns the table of
+// thread mappings those families contain.
 #include "hisq_internal.cuh"
 
 namespace hisq {
 
-cudaError_t dslash_f64_18_18(const DslashArgs&, int, int, int, int, cudaStream_t);
-cudaError_t dslash_f32_18_18(const DslashArgs&, int, int, int, int, cudaStream_t);
-cudaError_t dslash_f32_18_14(const DslashArgs&, int, int, int, int, cudaStream_t);
-cudaError_t dslash_f32_12_14(const DslashArgs&, int, int, int, int, cudaStream_t);
-cudaError_t dslash_f32_14_14(const DslashArgs&, int, int, int, int, cudaStream_t);
-cudaError_t dslash_f16_18_18(const DslashArgs&, int, int, int, int, cudaStream_t);
-cudaError_t dslash_f16_18_14(const DslashArgs&, int, int, int, int, cudaStream_t);
-cudaError_t dslash_f16_12_14(const DslashArgs&, int, int, int, int, cudaStream_t);
-cudaError_t dslash_f16_14_14(const DslashArgs&, int, int, int, int, cudaStream_t);
+#define HISQ_FAMILY_DECL(name) \
+    cudaError_t name(const DslashArgs&, int epi, int rpt, int minb, int pack, int layout, cudaStream_t)
+HISQ_FAMILY_DECL(dslash_f64_18_18);
+HISQ_FAMILY_DECL(dslash_f32_18_18);
+HISQ_FAMILY_DECL(dslash_f32_18_14);
+HISQ_FAMILY_DECL(dslash_f32_12_14);
+HISQ_FAMILY_DECL(dslash_f32_14_14);
+HISQ_FAMILY_DECL(dslash_f16_18_18);
+HISQ_FAMILY_DECL(dslash_f16_18_14);
+HISQ_FAMILY_DECL(dslash_f16_12_14);
+HISQ_FAMILY_DECL(dslash_f16_14_14);
+#undef HISQ_FAMILY_DECL
 
 int dslash_max_rpt(int prec) { return prec == HISQ_F64 ? 4 : 8; }
 
-// (rpt, minb) pairs compiled in dslash_inst.cu, default first
-bool dslash_mapping_built(int prec, int rpt, int minb) {
-    const int key = rpt * 10 + minb;
-    if (prec == HISQ_F64) return key == 12 || key == 22 || key == 41;
-    return key == 14 || key == 23 || key == 42 || key == 43 || key == 82;
+// (rpt, minb, pack) triples compiled in dslash_inst.cu
+bool dslash_mapping_built(int prec, int rpt, int minb, int pack) {
+    const int key = rpt * 100 + minb * 10 + pack;
+    if (prec == HISQ_F64) return key == 120 || key == 220 || key == 410;
+    switch (key) {
+        case 140: case 230: case 231: case 420: case 421: case 430: case 820: case 821:
+            return true;
+        default:
+            return false;
+    }
 }
 
-int dslash_default_minb(int prec, int rpt) {
-    if (prec == HISQ_F64) return rpt == 1 ? 2 : rpt == 2 ? 2 : rpt == 4 ? 1 : 0;
-    return rpt == 1 ? 4 : rpt == 2 ? 3 : rpt == 4 ? 2 : rpt == 8 ? 2 : 0;
+// Default register budget and arithmetic for an rpt (measured on GB300 at
+// 32^3x8 and 48^3x12, n = 8, FP32).
+DslashTune dslash_default_tune(int prec, int rpt, int layout) {
+    DslashTune t;
+    t.rpt = rpt;
+    t.layout = layout;
+    t.pack = 0;
+    t.prefetch = 0;
+    if (prec == HISQ_F64) {
+        t.minb = rpt == 4 ? 1 : 2;
+    } else {
+        t.minb = rpt == 1 ? 4 : rpt == 2 ? 3 : 2;
+    }
+    return t;
 }
 
 bool dslash_variant_supported(int prec, int ru, int rn, int epi) {
@@ -39,23 +59,29 @@ bool dslash_variant_supported(int prec, int ru, int rn, int epi) {
 cudaError_t launch_dslash(const DslashArgs& a, int prec, int ru, int rn, int epi,
                           const DslashTune& t, cudaStream_t s) {
     if (!dslash_variant_supported(prec, ru, rn, epi)) return cudaErrorInvalidValue;
-    if (!dslash_mapping_built(prec, t.rpt, t.minb)) return cudaErrorInvalidValue;
-    const int r = t.rpt, b = t.minb, l = t.layout;
-    if (prec == HISQ_F64) return dslash_f64_18_18(a, epi, r, b, l, s);
+    if (!dslash_mapping_built(prec, t.rpt, t.minb, t.pack)) return cudaErrorInvalidValue;
+    const int r = t.rpt, b = t.minb, pk = t.pack, l = t.layout;
+    if (t.prefetch != a.l2_prefetch) {
+        DslashArgs c = a;
+        c.l2_prefetch = t.prefetch;
+        DslashTune u = t;
+        return launch_dslash(c, prec, ru, rn, epi, u, s);
+    }
+    if (prec == HISQ_F64) return dslash_f64_18_18(a, epi, r, b, pk, l, s);
     const int key = ru * 100 + rn;
     if (prec == HISQ_F32) {
         switch (key) {
-            case 1818: return dslash_f32_18_18(a, epi, r, b, l, s);
-            case 1814: return dslash_f32_18_14(a, epi, r, b, l, s);
-            case 1214: return dslash_f32_12_14(a, epi, r, b, l, s);
-            case 1414: return dslash_f32_14_14(a, epi, r, b, l, s);
+            case 1818: return dslash_f32_18_18(a, epi, r, b, pk, l, s);
+            case 1814: return dslash_f32_18_14(a, epi, r, b, pk, l, s);
+            case 1214: return dslash_f32_12_14(a, epi, r, b, pk, l, s);
+            case 1414: return dslash_f32_14_14(a, epi, r, b, pk, l, s);
         }
     } else {
         switch (key) {
-            case 1818: return dslash_f16_18_18(a, epi, r, b, l, s);
-            case 1814: return dslash_f16_18_14(a, epi, r, b, l, s);
-            case 1214: return dslash_f16_12_14(a, epi, r, b, l, s);
-            case 1414: return dslash_f16_14_14(a, epi, r, b, l, s);
+            case 1818: return dslash_f16_18_18(a, epi, r, b, pk, l, s);
+            case 1814: return dslash_f16_18_14(a, epi, r, b, pk, l, s);
+            case 1214: return dslash_f16_12_14(a, epi, r, b, pk, l, s);
+            case 1414: return dslash_f16_14_14(a, epi, r, b, pk, l, s);
         }
     }
     return cudaErrorInvalidValue;

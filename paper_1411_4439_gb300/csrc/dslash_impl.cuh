@@ -153,14 +153,129 @@ __device__ __forceinline__ void mv_sub_dag(RC (&acc)[3], const Link<RC>& m, cons
         for (int j = 0; j < 3; ++j) cmsub_conj(acc[i], m.e[3 * j + i], v[j]);
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32 (f32x2) complex arithmetic: a complex multiply-add is two
+// fma.rn.f32x2 on (re, im) pairs instead of four scalar FMAs.
+//   a*b   = (a.x, a.x) * (b.x, b.y) + (-a.y, a.y) * (b.y, b.x)
+//  -a^* b = (-a.x, -a.x) * (b.x, b.y) + (-a.y, a.y) * (b.y, b.x)
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2x;
+
+__device__ __forceinline__ f2x pk2(float lo, float hi) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 up2(f2x v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+    f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Link elements as the two packed factors above; sgn = +1 forward, -1 for
+// the daggered backward hop (which also reads element (j, i)).
+struct PLink {
+    f2x p1[9];
+    f2x p2[9];
+};
+
+__device__ __forceinline__ void pack_link(PLink& pl, const Link<float2>& m, float sgn) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        pl.p1[e] = pk2(sgn * m.e[e].x, sgn * m.e[e].x);
+        pl.p2[e] = pk2(-m.e[e].y, m.e[e].y);
+    }
+}
+
+// acc[i] += sum_j m_ij v_j (fwd) or acc[i] -= sum_j conj(m_ji) v_j (bwd)
+template <bool DAG>
+__device__ __forceinline__ void mv_packed(f2x (&acc)[3], const PLink& pl, const float2 (&v)[3]) {
+    f2x b1[3], b2[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        b1[j] = pk2(v[j].x, v[j].y);
+        b2[j] = pk2(v[j].y, v[j].x);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int e = DAG ? 3 * j + i : 3 * i + j;
+            acc[i] = fma2(pl.p1[e], b1[j], acc[i]);
+            acc[i] = fma2(pl.p2[e], b2[j], acc[i]);
+        }
+}
+
+// Asynchronous bulk prefetch of [elem0, elem1) of one link component slab
+// into L2 (no registers, no completion to wait for). The range is clamped to
+// the slab and widened to 16-byte boundaries.
+template <typename LC>
+__device__ __forceinline__ void prefetch_slab(const LC* slab, int vh, long long elem0, long long elem1) {
+    if (elem0 < 0) elem0 = 0;
+    if (elem1 > vh) elem1 = vh;
+    if (elem1 <= elem0) return;
+    uintptr_t b0 = reinterpret_cast<uintptr_t>(slab + elem0) & ~(uintptr_t)15;
+    uintptr_t b1 = (reinterpret_cast<uintptr_t>(slab + elem1) + 15) & ~(uintptr_t)15;
+    const uintptr_t lim = reinterpret_cast<uintptr_t>(slab + vh) & ~(uintptr_t)15;
+    if (b1 > lim) b1 = lim;
+    if (b1 <= b0) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"((unsigned)(b1 - b0))
+                 : "memory");
+}
+
+// Lanes of the first warp prefetch into L2 the links that the block's sites
+// [hb, hb + nb) read: forward links of those sites and backward links of
+// their neighbours (shifted ranges; wrapped neighbours are not covered).
+template <typename LC, int NCU, int NCN>
+__device__ __forceinline__ void prefetch_tile_links(const LC* Ub, const LC* Nb, const Geom& g, int p,
+                                                    int hb, int nb) {
+    if (threadIdx.y != 0 || threadIdx.x >= 32) return;
+    const int q = 1 - p;
+    const int vh = g.vh;
+    constexpr int per_dir = 2 * (NCU + NCN);
+    for (int job = threadIdx.x; job < 4 * per_dir; job += 32) {
+        const int mu = job / per_dir;
+        int r = job - mu * per_dir;
+        const bool naik = r >= 2 * NCU;
+        if (naik) r -= 2 * NCU;
+        const int nc = naik ? NCN : NCU;
+        const bool back = r >= nc;
+        const int c = back ? r - nc : r;
+        const LC* base = naik ? Nb : Ub;
+        const int par = back ? q : p;
+        const LC* slab = base + ((size_t)(par * 4 + mu) * nc + c) * vh;
+        long long e0 = hb, e1 = (long long)hb + nb;
+        if (back) {
+            const int d = naik ? 3 : 1;
+            if (mu == 0) {
+                e0 -= g.hx;
+                e1 += g.hx;
+            } else {
+                const int s = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
+                e0 -= (long long)d * s;
+                e1 -= (long long)d * s;
+            }
+        }
+        prefetch_slab(slab, vh, e0, e1);
+    }
+}
+
 __device__ __forceinline__ int wrap(int c, int L) {
     c = (c >= L) ? c - L : c;
     return (c < 0) ? c + L : c;
 }
 
-template <typename S, typename LS, int RU, int RN, int RPT, int MINB, int EPI, int LAYOUT>
+template <typename S, typename LS, int RU, int RN, int RPT, int MINB, int EPI, int LAYOUT, bool PACK>
 __global__ void __launch_bounds__(256, MINB) dslash_kernel(const DslashArgs a) {
     using R = typename Traits<S>::R;
+    static_assert(!PACK || sizeof(R) == 4, "packed f32x2 arithmetic needs FP32 accumulation");
     using RC = typename Cx<R>::T;
     using SC = typename Traits<S>::C;
     using LC = typename Traits<LS>::C;
@@ -182,7 +297,14 @@ __global__ void __launch_bounds__(256, MINB) dslash_kernel(const DslashArgs a) {
         red1[j] = (R)0;
     }
 
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < vh; h += gridDim.x * blockDim.x) {
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h - (int)threadIdx.x < vh;
+         h += gridDim.x * blockDim.x) {
+        if (a.l2_prefetch) {
+            // pull this tile's links into L2 at full bandwidth while the first
+            // hops wait on their own loads; later hops then hit in L2
+            prefetch_tile_links<LC, NCU, NCN>(Ub, Nb, g, p, h - (int)threadIdx.x, blockDim.x);
+        }
+        if (h >= vh) continue;
         // coordinates of output site h of parity p
         const int xh = h % g.hx;
         int r = h / g.hx;
@@ -194,12 +316,14 @@ __global__ void __launch_bounds__(256, MINB) dslash_kernel(const DslashArgs a) {
         const int hrow = h - xh;
 
         RC acc[RPT][3];
+        f2x accp[PACK ? RPT : 1][3];
 #pragma unroll
         for (int j = 0; j < RPT; ++j)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 acc[j][c].x = (R)0;
                 acc[j][c].y = (R)0;
+                if constexpr (PACK) accp[j][c] = pk2(0.f, 0.f);
             }
 
 #pragma unroll
@@ -240,16 +364,40 @@ __global__ void __launch_bounds__(256, MINB) dslash_kernel(const DslashArgs a) {
                     const double f = (hop == 0) ? a.ft1 : (hop == 1) ? a.bt1 : (hop == 2) ? a.ft3 : a.bt3;
                     scale_link(m, (R)f);
                 }
+                if constexpr (PACK) {
+                    PLink pl;
+                    pack_link(pl, m, (hop == 0 || hop == 2) ? 1.f : -1.f);
 #pragma unroll
-                for (int j = 0; j < RPT; ++j) {
-                    RC v[3];
-                    load_spinor<SC, LAYOUT, RC>(v, a.in[k0 + j], hn, vh);
-                    if (hop == 0 || hop == 2)
-                        mv_add(acc[j], m, v);
-                    else
-                        mv_sub_dag(acc[j], m, v);
+                    for (int j = 0; j < RPT; ++j) {
+                        float2 v[3];
+                        load_spinor<SC, LAYOUT, float2>(v, a.in[k0 + j], hn, vh);
+                        if (hop == 0 || hop == 2)
+                            mv_packed<false>(accp[j], pl, v);
+                        else
+                            mv_packed<true>(accp[j], pl, v);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) {
+                        RC v[3];
+                        load_spinor<SC, LAYOUT, RC>(v, a.in[k0 + j], hn, vh);
+                        if (hop == 0 || hop == 2)
+                            mv_add(acc[j], m, v);
+                        else
+                            mv_sub_dag(acc[j], m, v);
+                    }
                 }
             }
+        }
+        if constexpr (PACK) {
+#pragma unroll
+            for (int j = 0; j < RPT; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 u = up2(accp[j][c]);
+                    acc[j][c].x = u.x;
+                    acc[j][c].y = u.y;
+                }
         }
 
         // epilogue
@@ -343,14 +491,14 @@ __global__ void __launch_bounds__(256, MINB) dslash_kernel(const DslashArgs a) {
 // ---------------------------------------------------------------------------
 // Host-side launcher for one instance
 // ---------------------------------------------------------------------------
-template <typename S, typename LS, int RU, int RN, int RPT, int MINB, int EPI, int LAYOUT>
+template <typename S, typename LS, int RU, int RN, int RPT, int MINB, int EPI, int LAYOUT, bool PACK>
 cudaError_t launch_dslash_instance(const DslashArgs& a, cudaStream_t s) {
     const int G = a.nrhs / RPT;
     if (G < 1 || G * RPT != a.nrhs || G > 8) return cudaErrorInvalidValue;
     int bx = 256 / G;
     bx &= ~31;
     const dim3 block(bx, G);
-    auto* kern = dslash_kernel<S, LS, RU, RN, RPT, MINB, EPI, LAYOUT>;
+    auto* kern = dslash_kernel<S, LS, RU, RN, RPT, MINB, EPI, LAYOUT, PACK>;
     static int occ_cache[9] = {0};
     int occ = occ_cache[G];
     if (occ == 0) {

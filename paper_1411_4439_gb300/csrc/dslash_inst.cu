@@ -2,8 +2,10 @@
 //
 // This file is compiled once per family with
 //   -DHISQ_STORE=<double|float|__half> -DHISQ_RU=<18|12|14> -DHISQ_RN=<18|14>
-//   -DHISQ_FAMILY=<function name>
-// so the families build in parallel translation units.
+//   -DHISQ_FAMILY=<function name> -DHISQ_MAX_RPT=<4|8> -DHISQ_WITH_XY=<0|1>
+// so the families build in parallel translation units. Each family holds the
+// thread mappings (rhs per thread, minimum resident blocks, packed f32x2
+// arithmetic) listed in dslash_dispatch.cu, for both spinor layouts.
 #include "dslash_impl.cuh"
 
 #if !defined(HISQ_STORE) || !defined(HISQ_RU) || !defined(HISQ_RN) || !defined(HISQ_FAMILY)
@@ -12,43 +14,54 @@
 
 namespace hisq {
 
+#define HISQ_INST(R, B, P) \
+    launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, R, B, EPI, LAYOUT, P>(a, s)
+
 template <int EPI, int LAYOUT>
-static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, cudaStream_t s) {
+static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, int pack,
+                                     cudaStream_t s) {
     using S = HISQ_STORE;
-    const int key = rpt * 10 + minb;
+    const int key = rpt * 100 + minb * 10 + pack;
     switch (key) {
 #if HISQ_MAX_RPT >= 8
-        // FP32 / FP16 storage
-        case 14: return launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, 1, 4, EPI, LAYOUT>(a, s);
-        case 23: return launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, 2, 3, EPI, LAYOUT>(a, s);
-        case 42: return launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, 4, 2, EPI, LAYOUT>(a, s);
-        case 43: return launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, 4, 3, EPI, LAYOUT>(a, s);
-        case 82: return launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, 8, 2, EPI, LAYOUT>(a, s);
+        // FP32 / FP16 storage, FP32 arithmetic
+        case 140: return HISQ_INST(1, 4, false);
+        case 230: return HISQ_INST(2, 3, false);
+        case 231: return HISQ_INST(2, 3, true);
+        case 420: return HISQ_INST(4, 2, false);
+        case 421: return HISQ_INST(4, 2, true);
+        case 430: return HISQ_INST(4, 3, false);
+        case 820: return HISQ_INST(8, 2, false);
+        case 821: return HISQ_INST(8, 2, true);
 #else
-        // FP64 storage
-        case 12: return launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, 1, 2, EPI, LAYOUT>(a, s);
-        case 22: return launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, 2, 2, EPI, LAYOUT>(a, s);
-        case 41: return launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, 4, 1, EPI, LAYOUT>(a, s);
+        // FP64 storage and arithmetic
+        case 120: return HISQ_INST(1, 2, false);
+        case 220: return HISQ_INST(2, 2, false);
+        case 410: return HISQ_INST(4, 1, false);
 #endif
         default: return cudaErrorInvalidValue;
     }
 }
+
+#undef HISQ_INST
 
 template <int LAYOUT>
-static cudaError_t family_by_epi(const DslashArgs& a, int epi, int rpt, int minb, cudaStream_t s) {
+static cudaError_t family_by_epi(const DslashArgs& a, int epi, int rpt, int minb, int pack,
+                                 cudaStream_t s) {
     switch (epi) {
-        case EPI_NONE: return family_by_variant<EPI_NONE, LAYOUT>(a, rpt, minb, s);
-        case EPI_X: return family_by_variant<EPI_X, LAYOUT>(a, rpt, minb, s);
+        case EPI_NONE: return family_by_variant<EPI_NONE, LAYOUT>(a, rpt, minb, pack, s);
+        case EPI_X: return family_by_variant<EPI_X, LAYOUT>(a, rpt, minb, pack, s);
 #if HISQ_WITH_XY
-        case EPI_XY: return family_by_variant<EPI_XY, LAYOUT>(a, rpt, minb, s);
+        case EPI_XY: return family_by_variant<EPI_XY, LAYOUT>(a, rpt, minb, pack, s);
 #endif
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t HISQ_FAMILY(const DslashArgs& a, int epi, int rpt, int minb, int layout, cudaStream_t s) {
-    return layout == HISQ_SOA ? family_by_epi<HISQ_SOA>(a, epi, rpt, minb, s)
-                              : family_by_epi<HISQ_AOS>(a, epi, rpt, minb, s);
+cudaError_t HISQ_FAMILY(const DslashArgs& a, int epi, int rpt, int minb, int pack, int layout,
+                        cudaStream_t s) {
+    return layout == HISQ_SOA ? family_by_epi<HISQ_SOA>(a, epi, rpt, minb, pack, s)
+                              : family_by_epi<HISQ_AOS>(a, epi, rpt, minb, pack, s);
 }
 
 }  // namespace hisq

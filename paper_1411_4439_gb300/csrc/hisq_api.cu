@@ -54,6 +54,10 @@ size_t prec_complex_bytes(int prec) {
 
 bool valid_prec(int p) { return p == HISQ_F64 || p == HISQ_F32 || p == HISQ_F16; }
 
+// Storage of the CG's low-precision solution increment: FP16 iterations keep
+// it in FP32 (see XType in blas.cu).
+int solution_prec(int prec) { return prec == HISQ_F16 ? HISQ_F32 : prec; }
+
 hisq_status make_geom(const int L[4], Geom* g) {
     if (L == nullptr) return fail(HISQ_EINVAL, "lattice extents pointer is NULL");
     long long V = 1;
@@ -162,6 +166,7 @@ struct hisq_gauge_s {
     size_t link_bytes = 0;
     int tune_rpt = 0;            // 0 = automatic
     int tune_minb = 0;
+    int tune_flags = 0;          // HISQ_MAP_* bits
     void* mdagm_tmp = nullptr;
     size_t mdagm_tmp_bytes = 0;
     double* dot_partials = nullptr;     // reduction scratch of hisq_cdot
@@ -320,13 +325,15 @@ extern "C" hisq_status hisq_gauge_info(hisq_gauge g, int L[4], hisq_prec* prec, 
     return HISQ_OK;
 }
 
-extern "C" hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rpt, int minb) {
+extern "C" hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rpt, int minb, int flags) {
     if (!g) return fail(HISQ_EINVAL, "NULL handle");
     if (rpt != 0 && rpt != 1 && rpt != 2 && rpt != 4 && rpt != 8)
         return fail(HISQ_EINVAL, "rhs per thread must be 0 (auto), 1, 2, 4 or 8");
     if (minb < 0 || minb > 8) return fail(HISQ_EINVAL, "min blocks per SM must be 0 (auto) .. 8");
+    if (flags & ~(HISQ_MAP_PACKED | HISQ_MAP_L2_PREFETCH)) return fail(HISQ_EINVAL, "unknown mapping flags %d", flags);
     g->tune_rpt = rpt;
     g->tune_minb = minb;
+    g->tune_flags = flags;
     return HISQ_OK;
 }
 
@@ -409,14 +416,15 @@ int auto_rpt(int n, int prec) {
 // Thread mapping for n rhs: the requested rpt, else the handle's setting,
 // else the largest power of two dividing n (at most 8 rhs groups per block).
 DslashTune pick_tune(hisq_gauge g, int n, int prec, int requested, int layout) {
-    DslashTune t;
-    t.layout = layout;
     int r = requested ? requested : g->tune_rpt;
     if (r == 0 || r > dslash_max_rpt(prec) || n % r != 0 || n / r > 8) r = auto_rpt(n, prec);
-    t.rpt = r;
-    int b = requested ? 0 : g->tune_minb;
-    if (b == 0 || !dslash_mapping_built(prec, r, b)) b = dslash_default_minb(prec, r);
-    t.minb = b;
+    DslashTune t = dslash_default_tune(prec, r, layout);
+    const int pack = (g->tune_flags & HISQ_MAP_PACKED) ? 1 : 0;
+    if (!requested && g->tune_minb && r == g->tune_rpt && dslash_mapping_built(prec, r, g->tune_minb, pack)) {
+        t.minb = g->tune_minb;
+        t.pack = pack;
+    }
+    if (g->tune_flags & HISQ_MAP_L2_PREFETCH) t.prefetch = 1;
     return t;
 }
 
@@ -541,8 +549,7 @@ extern "C" hisq_status hisq_apply_m(hisq_gauge g, double mass, double mu, int op
                                    hisq_prec spinor_prec, void* stream) {
     hisq_status st = check_spinors(g, v, w, n, spinor_prec);
     if (st != HISQ_OK) return st;
-    if (op != HISQ_OP_M && op != HISQ_OP_MDAG && op != HISQ_OP_DM_DMU)
-        return fail(HISQ_EINVAL, "unknown operator %d", op);
+    if (op < HISQ_OP_M || op > HISQ_OP_D4M_DMU4) return fail(HISQ_EINVAL, "unknown operator %d", op);
     if (!std::isfinite(mass) || !std::isfinite(mu)) return fail(HISQ_EINVAL, "mass and mu must be finite");
     const size_t half = (size_t)g->g.vh * 3 * prec_complex_bytes(spinor_prec);
     for (int k = 0; k < n; ++k)
@@ -573,13 +580,15 @@ extern "C" hisq_status hisq_apply_m(hisq_gauge g, double mass, double mu, int op
             a.cx = 2.0 * mass;
             a.cd = -1.0;
         } else {
-            // d/dmu of the temporal hops: +e^{mu} U v(x+t), +e^{-mu} U^dag v(x-t),
-            // +3 e^{3mu} N v(x+3t), +3 e^{-3mu} N^dag v(x-3t); the kernel subtracts
-            // the backward terms, so their factors carry a minus sign
+            // k-th mu-derivative of the temporal hops: e^{mu} U v(x+t),
+            // -(-1)^k e^{-mu} U^dag v(x-t), 3^k e^{3mu} N v(x+3t),
+            // -(-3)^k e^{-3mu} N^dag v(x-3t). The kernel subtracts the
+            // backward terms, so bt1 = (-1)^k e^{-mu} and bt3 = (-3)^k e^{-3mu}.
+            const int k = op - HISQ_OP_DM_DMU + 1;
             a.ft1 = std::exp(mu);
-            a.bt1 = -std::exp(-mu);
-            a.ft3 = 3.0 * std::exp(3.0 * mu);
-            a.bt3 = -3.0 * std::exp(-3.0 * mu);
+            a.bt1 = std::pow(-1.0, k) * std::exp(-mu);
+            a.ft3 = std::pow(3.0, k) * std::exp(3.0 * mu);
+            a.bt3 = std::pow(-3.0, k) * std::exp(-3.0 * mu);
             a.has_mu = 1;
             a.t_only = 1;
             epi = EPI_NONE;
@@ -672,6 +681,7 @@ hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** o
     w->len_half = 3ll * g->g.vh;
     w->len = full ? 2 * w->len_half : w->len_half;
     const size_t lo = (size_t)n * w->len * prec_complex_bytes(prec);
+    const size_t xlo = (size_t)n * w->len * prec_complex_bytes(solution_prec(prec));
     const size_t hi = (size_t)n * w->len * sizeof(double2);
     const size_t tlo = (size_t)n * w->len * prec_complex_bytes(prec);
     const size_t thi = (size_t)n * w->len * sizeof(double2);
@@ -685,7 +695,7 @@ hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** o
     al(&w->r_lo, lo);
     al(&w->p_lo, lo);
     al(&w->Ap_lo, lo);
-    al(&w->x_lo, lo);
+    al(&w->x_lo, xlo);
     al(&w->t_lo, tlo);
     al((void**)&w->b_hi, hi);
     al((void**)&w->x_hi, hi);
@@ -696,9 +706,10 @@ hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** o
     al((void**)&w->counter, sizeof(unsigned int) * 4);
     if (e == cudaSuccess) e = cudaMemset(w->counter, 0, sizeof(unsigned int) * 4);
     // vectors of rhs that never iterate must still hold finite numbers
-    void* zero_lo[] = {w->r_lo, w->p_lo, w->Ap_lo, w->x_lo, w->t_lo};
+    void* zero_lo[] = {w->r_lo, w->p_lo, w->Ap_lo, w->t_lo};
     for (void* z : zero_lo)
         if (e == cudaSuccess) e = cudaMemset(z, 0, lo);
+    if (e == cudaSuccess) e = cudaMemset(w->x_lo, 0, xlo);
     double2* zero_hi[] = {w->b_hi, w->x_hi, w->r_hi, w->t_hi};
     for (double2* z : zero_hi)
         if (e == cudaSuccess) e = cudaMemset(z, 0, hi);
@@ -986,7 +997,7 @@ extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const
         HISQ_CUDA(cudaMemsetAsync(w->x_hi, 0, vec_bytes * n, s));
     }
     HISQ_CUDA(cudaMemsetAsync(w->cg, 0, sizeof(CgScalars), s));
-    HISQ_CUDA(cudaMemsetAsync(w->x_lo, 0, (size_t)n * w->len * prec_complex_bytes(sv.prec), s));
+    HISQ_CUDA(cudaMemsetAsync(w->x_lo, 0, (size_t)n * w->len * prec_complex_bytes(solution_prec(sv.prec)), s));
     HISQ_CUDA(launch_norm_bb(sv.blas(), w->b_hi, s));
     if (prm.use_x0) {
         HISQ_CUDA(sv.true_residual(s));

@@ -100,6 +100,7 @@ struct CgScalars {
     int frozen[kMaxRhs];       // 1: residual fell below freeze2 * rr_rel; skip until the next reliable update
     int stall[kMaxRhs];        // 1: <p,Ap> <= 0 in low precision; this iteration restarts p = r
     int restarts[kMaxRhs];     // number of such restarts in this solve
+    int reset_p[kMaxRhs];      // 1: the reliable update restarts p = r (true and iterated residual disagree)
     double freeze2;            // squared residual drop that freezes an rhs (precision safety net)
     double alpha_max;          // alpha above this bound (1/lambda_min) means lost precision: restart
     int flags;                 // kFlagBreakdown | kFlagNaN
@@ -139,6 +140,7 @@ struct DslashArgs {
     double ft1, bt1, ft3, bt3;          // temporal hop factors e^{+mu}, e^{-mu}, e^{3mu}, e^{-3mu}
     int has_mu;                         // 1 if any factor differs from 1
     int t_only;                         // 1: temporal hops only (d D / d mu)
+    int l2_prefetch;                    // 1: bulk-prefetch each tile's links into L2
     double r12_inv_scale;               // 1 / s for R12 fat links
     int red_mode;
     int finish;
@@ -152,11 +154,14 @@ struct DslashArgs {
 enum Epi : int { EPI_NONE = 0, EPI_X = 1, EPI_XY = 2 };
 
 // Thread mapping and spinor layout of one launch: rpt rhs per thread,
-// compiled for at least minb resident 256-thread blocks per SM.
+// compiled for at least minb resident 256-thread blocks per SM, with packed
+// f32x2 complex arithmetic when pack = 1 (FP32 arithmetic only).
 struct DslashTune {
     int rpt;
     int minb;
-    int layout;   // HISQ_AOS or HISQ_SOA
+    int pack;
+    int layout;     // HISQ_AOS or HISQ_SOA
+    int prefetch;   // bulk L2 prefetch of each tile's links
 };
 
 // Dispatch into the instantiated kernels. prec is the spinor and link storage
@@ -164,9 +169,9 @@ struct DslashTune {
 cudaError_t launch_dslash(const DslashArgs& a, int prec, int ru, int rn, int epi,
                           const DslashTune& t, cudaStream_t s);
 bool dslash_variant_supported(int prec, int ru, int rn, int epi);
-// Built (rpt, minb) pairs of a precision, and the default minb for an rpt (0 if none).
-bool dslash_mapping_built(int prec, int rpt, int minb);
-int dslash_default_minb(int prec, int rpt);
+// Built (rpt, minb, pack) mappings of a precision, and the default one for an rpt.
+bool dslash_mapping_built(int prec, int rpt, int minb, int pack);
+DslashTune dslash_default_tune(int prec, int rpt, int layout);
 // Largest rhs-per-thread value instantiated for a precision.
 int dslash_max_rpt(int prec);
 

@@ -127,6 +127,15 @@ __device__ __forceinline__ void finish_reliable(CgScalars* cg, const double* val
     const int k = threadIdx.x + threadIdx.y * blockDim.x;
     if (k < n) {
         const double nrm = vals[2 * k], mx = vals[2 * k + 1];
+        // The search direction p is kept across the update while the
+        // iterated residual still describes the true one. Once the true
+        // residual is 10x (in norm) above the iterated one, the iteration has
+        // run into its rounding floor and p no longer belongs to this
+        // residual; a frozen rhs skipped its last p update. Both restart
+        // from p = r.
+        const double sc = cg->scale[k];
+        const double iterated = cg->rr[k] / (sc * sc);
+        cg->reset_p[k] = (nrm > 100.0 * iterated || cg->frozen[k]) ? 1 : 0;
         cg->rr_true[k] = nrm;
         cg->rmax[k] = mx;
         if (!isfinite(nrm)) {

@@ -35,6 +35,8 @@ STATUS_NAMES = {0: "HISQ_OK", 1: "HISQ_EINVAL", 2: "HISQ_ERECON", 3: "HISQ_ENOCO
 MAX_RHS = 16
 
 HISQ_OP_M, HISQ_OP_MDAG, HISQ_OP_DM_DMU = 0, 1, 2
+HISQ_OP_D2M_DMU2, HISQ_OP_D3M_DMU3, HISQ_OP_D4M_DMU4 = 3, 4, 5
+HISQ_MAP_PACKED, HISQ_MAP_L2_PREFETCH = 1, 2
 
 EXPORTED = ["hisq_version", "hisq_last_error", "hisq_gauge_load", "hisq_gauge_free",
             "hisq_gauge_info", "hisq_set_dslash_mapping", "hisq_link_compress",
@@ -84,7 +86,7 @@ def library() -> ctypes.CDLL:
                                     ctypes.POINTER(vp)]),
         "hisq_gauge_free": (c_int, [vp]),
         "hisq_gauge_info": (c_int, [vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_size_t)]),
-        "hisq_set_dslash_mapping": (c_int, [vp, c_int, c_int]),
+        "hisq_set_dslash_mapping": (c_int, [vp, c_int, c_int, c_int]),
         "hisq_link_compress": (c_int, [ip, vp, c_int, vp, ctypes.POINTER(c_double), vp]),
         "hisq_link_reconstruct": (c_int, [ip, vp, c_int, vp, vp]),
         "hisq_dslash": (c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int, c_int, vp]),
@@ -236,9 +238,12 @@ def hisq_gauge_info(g: Gauge) -> dict:
                 device_bytes=nbytes.value)
 
 
-def hisq_set_dslash_mapping(g: Gauge, rhs_per_thread: int, min_blocks: int = 0) -> None:
-    """Dslash rhs per thread and register budget (min blocks per SM); 0 = automatic."""
-    _check(library().hisq_set_dslash_mapping(g.handle, int(rhs_per_thread), int(min_blocks)))
+def hisq_set_dslash_mapping(g: Gauge, rhs_per_thread: int, min_blocks: int = 0,
+                            flags: int = 0) -> None:
+    """Dslash rhs per thread, register budget (min blocks per SM) and HISQ_MAP_* flags
+    (packed f32x2 arithmetic, L2 link prefetch); 0 = automatic."""
+    _check(library().hisq_set_dslash_mapping(g.handle, int(rhs_per_thread), int(min_blocks),
+                                             int(flags)))
 
 
 def hisq_link_compress(L, links, recon, packed, stream=None) -> float:

@@ -219,3 +219,16 @@ def test_full_size_config1_true_residual(gpu_lib):
     assert np.all(res <= 1e-10), res
     for k in range(8):
         assert abs(st.true_rel_res[k] - res[k]) <= 1e-11
+
+
+def test_aos_and_soa_solves_agree(gpu_lib):
+    H = gpu_lib
+    L, m = (4, 6, 8, 10), 0.03
+    U, N = gen.hisq_links(L, seed=19)
+    b = gen.z2_source(L, 3, seed=20)
+    xa, sa = solve(H, L, U, N, b, m, prec=1, spinor_layout=H.HISQ_AOS)
+    xs, ss = solve(H, L, U, N, b, m, prec=1, spinor_layout=H.HISQ_SOA)
+    xo, A = oracle_solution(U, N, L, b, m)
+    for x in (xa, xs):
+        assert np.all(O.true_relative_residual(A, x, b) <= 1e-10)
+        assert rel_l2(x, xo) <= 1e-8

@@ -362,3 +362,38 @@ def test_mu_derivative_is_finite_difference_of_dslash(mu_chem):
     w = gaussian_full(L, 2, 83)
     fd_dag = (O.apply_Mdag(U, N, w, 0.1, mu_chem + h) - O.apply_Mdag(U, N, w, 0.1, mu_chem - h)) / (2 * h)
     assert abs(np.vdot(v, fd_dag) - np.vdot(O.apply_dM_dmu(U, N, v, mu_chem), w)) < 1e-8 * np.linalg.norm(v) * np.linalg.norm(w)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_higher_mu_derivatives_are_finite_differences(order):
+    L = (4, 4, 4, 6)
+    U, N = gen.hisq_links(L, seed=84)
+    v = gaussian_full(L, 1, 85)
+    mu, h = 0.1, 1e-4
+    fd = (O.apply_dnM_dmun(U, N, v, mu + h, order - 1) - O.apply_dnM_dmun(U, N, v, mu - h, order - 1)) / (2 * h)
+    assert rel(O.apply_dnM_dmun(U, N, v, mu, order), fd) < 1e-6
+
+
+def test_trace_word_matches_dense_trace():
+    """With all unit vectors as noise the bilinear sum is the exact trace of the word."""
+    L, m, mu = (4, 4, 4, 4), 0.2, 0.1
+    U, N = gen.hisq_links(L, seed=86)
+    shape = O.grid_shape(L) + (3,)
+    dim = int(np.prod(shape))
+    Md = O.dense_matrix(lambda q: O.apply_M(U, N, q, m, mu), shape)
+    D1 = O.dense_matrix(lambda q: O.apply_dnM_dmun(U, N, q, mu, 1), shape)
+    D2 = O.dense_matrix(lambda q: O.apply_dnM_dmun(U, N, q, mu, 2), shape)
+    Mi = np.linalg.inv(Md)
+    exact_1 = np.trace(D1 @ Mi)
+    exact_11 = np.trace(D1 @ Mi @ D1 @ Mi)
+    exact_2 = np.trace(D2 @ Mi)
+    # a random subset of unit vectors gives the same partial sums as the dense matrices
+    rng = np.random.default_rng(87)
+    idx = rng.choice(dim, size=6, replace=False)
+    eta = np.zeros((6, dim), dtype=complex)
+    eta[np.arange(6), idx] = 1.0
+    eta = eta.reshape((6,) + shape)
+    for orders, W in (((1,), D1 @ Mi), ((1, 1), D1 @ Mi @ D1 @ Mi), ((2,), D2 @ Mi)):
+        got = O.trace_word_bilinear(U, N, eta, m, mu, orders)
+        assert np.allclose(got, W[idx, idx], rtol=1e-9, atol=1e-11)
+    assert abs(exact_1) > 0 and abs(exact_11) > 0 and abs(exact_2) > 0
