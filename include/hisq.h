@@ -129,13 +129,20 @@ hisq_status hisq_gauge_info(hisq_gauge g, int L[4], hisq_prec* prec,
  * thread (1, 2, 4, 8; FP64: 1, 2, 4) and the minimum resident blocks per SM
  * the kernel is compiled for (register budget); 0 = automatic. Flags:
  * HISQ_MAP_PACKED for paired FP32 (f32x2) complex arithmetic,
- * HISQ_MAP_L2_PREFETCH to bulk-prefetch each tile's links into L2. Mappings
- * that are not built, or rpt values that do not divide n, fall back to the
- * automatic choice.
+ * HISQ_MAP_L2_PREFETCH to bulk-prefetch each tile's links into L2,
+ * HISQ_MAP_STAGED to stage each tile's links in shared memory with bulk
+ * asynchronous copies (FP32/FP16 storage; tiles of 128 sites made of whole
+ * x-rows inside one y-z plane, at most 2 rhs groups). Mappings that are not
+ * built or do not fit n or the lattice fall back to the automatic choice.
  */
-enum { HISQ_MAP_PACKED = 1, HISQ_MAP_L2_PREFETCH = 2 };
+enum { HISQ_MAP_PACKED = 1, HISQ_MAP_L2_PREFETCH = 2, HISQ_MAP_STAGED = 4 };
 hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_blocks,
                                     int flags);
+
+/* The mapping a Dslash of n rhs in `spinor_prec` will use on this handle:
+ * rhs per thread, min blocks per SM and HISQ_MAP_* flags (host pointers). */
+hisq_status hisq_get_dslash_mapping(hisq_gauge g, int n, hisq_prec spinor_prec,
+                                    int* rhs_per_thread, int* min_blocks, int* flags);
 
 /*
  * Compress a canonical link field to `r` reals per link (R18/R14/R12, same

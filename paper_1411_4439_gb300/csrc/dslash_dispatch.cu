@@ -6,7 +6,7 @@
 namespace hisq {
 
 #define HISQ_FAMILY_DECL(name) \
-    cudaError_t name(const DslashArgs&, int epi, int rpt, int minb, int pack, int layout, cudaStream_t)
+    cudaError_t name(const DslashArgs&, int epi, int rpt, int minb, int kind, int layout, cudaStream_t)
 HISQ_FAMILY_DECL(dslash_f64_18_18);
 HISQ_FAMILY_DECL(dslash_f32_18_18);
 HISQ_FAMILY_DECL(dslash_f32_18_14);
@@ -20,25 +20,26 @@ HISQ_FAMILY_DECL(dslash_f16_14_14);
 
 int dslash_max_rpt(int prec) { return prec == HISQ_F64 ? 4 : 8; }
 
-// (rpt, minb, pack) triples compiled in dslash_inst.cu
-bool dslash_mapping_built(int prec, int rpt, int minb, int pack) {
-    const int key = rpt * 100 + minb * 10 + pack;
+// (rpt, minb, kind) triples compiled in dslash_inst.cu
+bool dslash_mapping_built(int prec, int rpt, int minb, int kind) {
+    const int key = rpt * 100 + minb * 10 + kind;
     if (prec == HISQ_F64) return key == 120 || key == 220 || key == 410;
     switch (key) {
         case 140: case 230: case 231: case 420: case 421: case 430: case 820: case 821:
+        case 422: case 432: case 822: case 832:
             return true;
         default:
             return false;
     }
 }
 
-// Default register budget and arithmetic for an rpt (measured on GB300 at
+// Default register budget and kernel kind for an rpt (measured on GB300 at
 // 32^3x8 and 48^3x12, n = 8, FP32).
 DslashTune dslash_default_tune(int prec, int rpt, int layout) {
     DslashTune t;
     t.rpt = rpt;
     t.layout = layout;
-    t.pack = 0;
+    t.kind = KIND_REG;
     t.prefetch = 0;
     if (prec == HISQ_F64) {
         t.minb = rpt == 4 ? 1 : 2;
@@ -46,6 +47,17 @@ DslashTune dslash_default_tune(int prec, int rpt, int layout) {
         t.minb = rpt == 1 ? 4 : rpt == 2 ? 3 : 2;
     }
     return t;
+}
+
+// Tiles of 128 sites must be whole x-rows inside one y-z plane, and every
+// row-sized bulk copy 16-byte aligned (see dslash_staged.cuh).
+bool dslash_staged_ok(const Geom& g, int prec, int rpt, int groups) {
+    if (prec != HISQ_F32 && prec != HISQ_F16) return false;
+    if (groups < 1 || groups > (rpt >= 8 ? 1 : 2)) return false;
+    const long long elem = prec == HISQ_F32 ? 8 : 4;
+    const int ts = 128;
+    return ts % g.hx == 0 && (g.hx * g.L[1]) % ts == 0 && (g.hx * elem) % 16 == 0 &&
+           ((long long)g.vh * elem) % 16 == 0;
 }
 
 bool dslash_variant_supported(int prec, int ru, int rn, int epi) {
@@ -59,29 +71,28 @@ bool dslash_variant_supported(int prec, int ru, int rn, int epi) {
 cudaError_t launch_dslash(const DslashArgs& a, int prec, int ru, int rn, int epi,
                           const DslashTune& t, cudaStream_t s) {
     if (!dslash_variant_supported(prec, ru, rn, epi)) return cudaErrorInvalidValue;
-    if (!dslash_mapping_built(prec, t.rpt, t.minb, t.pack)) return cudaErrorInvalidValue;
-    const int r = t.rpt, b = t.minb, pk = t.pack, l = t.layout;
+    if (!dslash_mapping_built(prec, t.rpt, t.minb, t.kind)) return cudaErrorInvalidValue;
     if (t.prefetch != a.l2_prefetch) {
         DslashArgs c = a;
         c.l2_prefetch = t.prefetch;
-        DslashTune u = t;
-        return launch_dslash(c, prec, ru, rn, epi, u, s);
+        return launch_dslash(c, prec, ru, rn, epi, t, s);
     }
-    if (prec == HISQ_F64) return dslash_f64_18_18(a, epi, r, b, pk, l, s);
+    const int r = t.rpt, b = t.minb, k = t.kind, l = t.layout;
+    if (prec == HISQ_F64) return dslash_f64_18_18(a, epi, r, b, k, l, s);
     const int key = ru * 100 + rn;
     if (prec == HISQ_F32) {
         switch (key) {
-            case 1818: return dslash_f32_18_18(a, epi, r, b, pk, l, s);
-            case 1814: return dslash_f32_18_14(a, epi, r, b, pk, l, s);
-            case 1214: return dslash_f32_12_14(a, epi, r, b, pk, l, s);
-            case 1414: return dslash_f32_14_14(a, epi, r, b, pk, l, s);
+            case 1818: return dslash_f32_18_18(a, epi, r, b, k, l, s);
+            case 1814: return dslash_f32_18_14(a, epi, r, b, k, l, s);
+            case 1214: return dslash_f32_12_14(a, epi, r, b, k, l, s);
+            case 1414: return dslash_f32_14_14(a, epi, r, b, k, l, s);
         }
     } else {
         switch (key) {
-            case 1818: return dslash_f16_18_18(a, epi, r, b, pk, l, s);
-            case 1814: return dslash_f16_18_14(a, epi, r, b, pk, l, s);
-            case 1214: return dslash_f16_12_14(a, epi, r, b, pk, l, s);
-            case 1414: return dslash_f16_14_14(a, epi, r, b, pk, l, s);
+            case 1818: return dslash_f16_18_18(a, epi, r, b, k, l, s);
+            case 1814: return dslash_f16_18_14(a, epi, r, b, k, l, s);
+            case 1214: return dslash_f16_12_14(a, epi, r, b, k, l, s);
+            case 1414: return dslash_f16_14_14(a, epi, r, b, k, l, s);
         }
     }
     return cudaErrorInvalidValue;

@@ -272,6 +272,13 @@ __device__ __forceinline__ int wrap(int c, int L) {
     return (c < 0) ? c + L : c;
 }
 
+template <typename SC, int RPT, int EPI, int LAYOUT, typename R, typename RC>
+__device__ __forceinline__ void epilogue_site(const DslashArgs& a, int h, int k0, const RC (&acc)[RPT][3],
+                                              R (&red0)[RPT], R (&red1)[RPT]);
+template <int RPT, typename R>
+__device__ __forceinline__ void block_reduce_finish(const DslashArgs& a, int k0, R (&red0)[RPT],
+                                                    R (&red1)[RPT]);
+
 template <typename S, typename LS, int RU, int RN, int RPT, int MINB, int EPI, int LAYOUT, bool PACK>
 __global__ void __launch_bounds__(256, MINB) dslash_kernel(const DslashArgs a) {
     using R = typename Traits<S>::R;
@@ -400,58 +407,73 @@ __global__ void __launch_bounds__(256, MINB) dslash_kernel(const DslashArgs a) {
                 }
         }
 
-        // epilogue
-#pragma unroll
-        for (int j = 0; j < RPT; ++j) {
-            const int k = k0 + j;
-            RC w[3];
-            if (EPI == EPI_NONE) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) w[c] = acc[j][c];
-            } else {
-                RC xv[3];
-                load_spinor<SC, LAYOUT, RC>(xv, a.x[k], h, vh);
-                const R cx = (R)a.cx, cd = (R)a.cd;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    w[c].x = fma(cd, acc[j][c].x, cx * xv[c].x);
-                    w[c].y = fma(cd, acc[j][c].y, cx * xv[c].y);
-                }
-                if (EPI == EPI_XY) {
-                    RC yv[3];
-                    load_spinor<SC, LAYOUT, RC>(yv, a.y[k], h, vh);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        w[c].x += yv[c].x;
-                        w[c].y += yv[c].y;
-                    }
-                }
-                if (a.red_mode == RED_DOT_XW) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        red0[j] = fma(xv[c].x, w[c].x, red0[j]);
-                        red0[j] = fma(xv[c].y, w[c].y, red0[j]);
-                    }
-                }
-            }
-            SC* o = reinterpret_cast<SC*>(a.out[k]);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) st_c(o + spinor_index<LAYOUT>(h, c, vh), w[c]);
-            if (a.red_mode == RED_NORM_MAX_W) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    // reduce what was stored, so the norm matches the stored vector
-                    const RC sv = stored_value(w[c], (const SC*)o);
-                    const R n2 = sv.x * sv.x + sv.y * sv.y;
-                    red0[j] += n2;
-                    red1[j] = fmax(red1[j], sqrt(n2));
-                }
-            }
-        }
+        epilogue_site<SC, RPT, EPI, LAYOUT>(a, h, k0, acc, red0, red1);
     }
 
     if (a.red_mode == RED_NONE) return;
+    block_reduce_finish<RPT>(a, k0, red0, red1);
+}
 
+// Epilogue of one output site: out = [y] + cx x + cd (D in) for the thread's
+// RPT rhs, stored in the spinor layout, with the per-thread reduction terms.
+template <typename SC, int RPT, int EPI, int LAYOUT, typename R, typename RC>
+__device__ __forceinline__ void epilogue_site(const DslashArgs& a, int h, int k0, const RC (&acc)[RPT][3],
+                                              R (&red0)[RPT], R (&red1)[RPT]) {
+    const int vh = a.g.vh;
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int k = k0 + j;
+        RC w[3];
+        if (EPI == EPI_NONE) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) w[c] = acc[j][c];
+        } else {
+            RC xv[3];
+            load_spinor<SC, LAYOUT, RC>(xv, a.x[k], h, vh);
+            const R cx = (R)a.cx, cd = (R)a.cd;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                w[c].x = fma(cd, acc[j][c].x, cx * xv[c].x);
+                w[c].y = fma(cd, acc[j][c].y, cx * xv[c].y);
+            }
+            if (EPI == EPI_XY) {
+                RC yv[3];
+                load_spinor<SC, LAYOUT, RC>(yv, a.y[k], h, vh);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    w[c].x += yv[c].x;
+                    w[c].y += yv[c].y;
+                }
+            }
+            if (a.red_mode == RED_DOT_XW) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    red0[j] = fma(xv[c].x, w[c].x, red0[j]);
+                    red0[j] = fma(xv[c].y, w[c].y, red0[j]);
+                }
+            }
+        }
+        SC* o = reinterpret_cast<SC*>(a.out[k]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st_c(o + spinor_index<LAYOUT>(h, c, vh), w[c]);
+        if (a.red_mode == RED_NORM_MAX_W) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                // reduce what was stored, so the norm matches the stored vector
+                const RC sv = stored_value(w[c], (const SC*)o);
+                const R n2 = sv.x * sv.x + sv.y * sv.y;
+                red0[j] += n2;
+                red1[j] = fmax(red1[j], sqrt(n2));
+            }
+        }
+    }
+}
+
+// Per-rhs block reduction (warp tree -> shared -> partial slot) and the
+// last-block finish. Called by every thread of the block.
+template <int RPT, typename R>
+__device__ __forceinline__ void block_reduce_finish(const DslashArgs& a, int k0, R (&red0)[RPT],
+                                                    R (&red1)[RPT]) {
     // per-rhs block reduction: warp (fixed tree) -> shared -> partial slot
     __shared__ double s_part[kMaxRedVals][8];
     __shared__ double s_vals[kMaxRedVals];

@@ -4,9 +4,11 @@
 //   -DHISQ_STORE=<double|float|__half> -DHISQ_RU=<18|12|14> -DHISQ_RN=<18|14>
 //   -DHISQ_FAMILY=<function name> -DHISQ_MAX_RPT=<4|8> -DHISQ_WITH_XY=<0|1>
 // so the families build in parallel translation units. Each family holds the
-// thread mappings (rhs per thread, minimum resident blocks, packed f32x2
-// arithmetic) listed in dslash_dispatch.cu, for both spinor layouts.
-#include "dslash_impl.cuh"
+// thread mappings (rhs per thread, minimum resident blocks, kernel kind)
+// listed in dslash_dispatch.cu, for both spinor layouts. Kinds: 0 register
+// kernel, 1 register kernel with packed f32x2 arithmetic, 2 links staged in
+// shared memory by bulk copies.
+#include "dslash_staged.cuh"
 
 #if !defined(HISQ_STORE) || !defined(HISQ_RU) || !defined(HISQ_RN) || !defined(HISQ_FAMILY)
 #error "dslash_inst.cu needs HISQ_STORE, HISQ_RU, HISQ_RN and HISQ_FAMILY"
@@ -16,12 +18,13 @@ namespace hisq {
 
 #define HISQ_INST(R, B, P) \
     launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, R, B, EPI, LAYOUT, P>(a, s)
+#define HISQ_STAGED(R, B) launch_dslash_staged<S, S, HISQ_RU, HISQ_RN, R, B, EPI, LAYOUT>(a, s)
 
 template <int EPI, int LAYOUT>
-static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, int pack,
+static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, int kind,
                                      cudaStream_t s) {
     using S = HISQ_STORE;
-    const int key = rpt * 100 + minb * 10 + pack;
+    const int key = rpt * 100 + minb * 10 + kind;
     switch (key) {
 #if HISQ_MAX_RPT >= 8
         // FP32 / FP16 storage, FP32 arithmetic
@@ -33,6 +36,10 @@ static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, int
         case 430: return HISQ_INST(4, 3, false);
         case 820: return HISQ_INST(8, 2, false);
         case 821: return HISQ_INST(8, 2, true);
+        case 422: return HISQ_STAGED(4, 2);
+        case 432: return HISQ_STAGED(4, 3);
+        case 822: return HISQ_STAGED(8, 2);
+        case 832: return HISQ_STAGED(8, 3);
 #else
         // FP64 storage and arithmetic
         case 120: return HISQ_INST(1, 2, false);
@@ -44,24 +51,25 @@ static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, int
 }
 
 #undef HISQ_INST
+#undef HISQ_STAGED
 
 template <int LAYOUT>
-static cudaError_t family_by_epi(const DslashArgs& a, int epi, int rpt, int minb, int pack,
+static cudaError_t family_by_epi(const DslashArgs& a, int epi, int rpt, int minb, int kind,
                                  cudaStream_t s) {
     switch (epi) {
-        case EPI_NONE: return family_by_variant<EPI_NONE, LAYOUT>(a, rpt, minb, pack, s);
-        case EPI_X: return family_by_variant<EPI_X, LAYOUT>(a, rpt, minb, pack, s);
+        case EPI_NONE: return family_by_variant<EPI_NONE, LAYOUT>(a, rpt, minb, kind, s);
+        case EPI_X: return family_by_variant<EPI_X, LAYOUT>(a, rpt, minb, kind, s);
 #if HISQ_WITH_XY
-        case EPI_XY: return family_by_variant<EPI_XY, LAYOUT>(a, rpt, minb, pack, s);
+        case EPI_XY: return family_by_variant<EPI_XY, LAYOUT>(a, rpt, minb, kind, s);
 #endif
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t HISQ_FAMILY(const DslashArgs& a, int epi, int rpt, int minb, int pack, int layout,
+cudaError_t HISQ_FAMILY(const DslashArgs& a, int epi, int rpt, int minb, int kind, int layout,
                         cudaStream_t s) {
-    return layout == HISQ_SOA ? family_by_epi<HISQ_SOA>(a, epi, rpt, minb, pack, s)
-                              : family_by_epi<HISQ_AOS>(a, epi, rpt, minb, pack, s);
+    return layout == HISQ_SOA ? family_by_epi<HISQ_SOA>(a, epi, rpt, minb, kind, s)
+                              : family_by_epi<HISQ_AOS>(a, epi, rpt, minb, kind, s);
 }
 
 }  // namespace hisq

@@ -330,7 +330,8 @@ extern "C" hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rpt, int minb, 
     if (rpt != 0 && rpt != 1 && rpt != 2 && rpt != 4 && rpt != 8)
         return fail(HISQ_EINVAL, "rhs per thread must be 0 (auto), 1, 2, 4 or 8");
     if (minb < 0 || minb > 8) return fail(HISQ_EINVAL, "min blocks per SM must be 0 (auto) .. 8");
-    if (flags & ~(HISQ_MAP_PACKED | HISQ_MAP_L2_PREFETCH)) return fail(HISQ_EINVAL, "unknown mapping flags %d", flags);
+    if (flags & ~(HISQ_MAP_PACKED | HISQ_MAP_L2_PREFETCH | HISQ_MAP_STAGED))
+        return fail(HISQ_EINVAL, "unknown mapping flags %d", flags);
     g->tune_rpt = rpt;
     g->tune_minb = minb;
     g->tune_flags = flags;
@@ -419,14 +420,35 @@ DslashTune pick_tune(hisq_gauge g, int n, int prec, int requested, int layout) {
     int r = requested ? requested : g->tune_rpt;
     if (r == 0 || r > dslash_max_rpt(prec) || n % r != 0 || n / r > 8) r = auto_rpt(n, prec);
     DslashTune t = dslash_default_tune(prec, r, layout);
-    const int pack = (g->tune_flags & HISQ_MAP_PACKED) ? 1 : 0;
-    if (!requested && g->tune_minb && r == g->tune_rpt && dslash_mapping_built(prec, r, g->tune_minb, pack)) {
+    int kind = KIND_REG;
+    if (g->tune_flags & HISQ_MAP_PACKED) kind = KIND_PACKED;
+    if (g->tune_flags & HISQ_MAP_STAGED) kind = KIND_STAGED;
+    if (!requested && g->tune_minb && r == g->tune_rpt && dslash_mapping_built(prec, r, g->tune_minb, kind) &&
+        (kind != KIND_STAGED || dslash_staged_ok(g->g, prec, r, n / r))) {
         t.minb = g->tune_minb;
-        t.pack = pack;
+        t.kind = kind;
     }
     if (g->tune_flags & HISQ_MAP_L2_PREFETCH) t.prefetch = 1;
     return t;
 }
+
+}  // namespace
+
+extern "C" hisq_status hisq_get_dslash_mapping(hisq_gauge g, int n, hisq_prec prec, int* rpt, int* minb,
+                                              int* flags) {
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
+    if (!valid_prec(prec)) return fail(HISQ_EINVAL, "unknown precision %d", prec);
+    const DslashTune t = pick_tune(g, n, prec, 0, HISQ_AOS);
+    if (rpt) *rpt = t.rpt;
+    if (minb) *minb = t.minb;
+    if (flags)
+        *flags = (t.kind == KIND_PACKED ? HISQ_MAP_PACKED : 0) | (t.kind == KIND_STAGED ? HISQ_MAP_STAGED : 0) |
+                 (t.prefetch ? HISQ_MAP_L2_PREFETCH : 0);
+    return HISQ_OK;
+}
+
+namespace {
 
 bool aligned_for(const void* p, int prec) {
     return ((uintptr_t)p % prec_complex_bytes(prec)) == 0;
@@ -763,6 +785,7 @@ struct Solver {
         a.red.partials = w->partials;
         a.red.counter = w->counter;
         a.cg = w->cg;
+        a.status = &w->cg->flags;
         a.tol2 = tol2;
         return a;
     }

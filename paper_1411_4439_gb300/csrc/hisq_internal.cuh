@@ -72,6 +72,10 @@ __device__ __forceinline__ float2 stored_value(float2 v, const __half2*) {
     return __half22float2(__float22half2_rn(v));
 }
 
+__device__ __forceinline__ double2 to_float2_or_double2(double2 v) { return v; }
+__device__ __forceinline__ float2 to_float2_or_double2(float2 v) { return v; }
+__device__ __forceinline__ float2 to_float2_or_double2(__half2 v) { return __half22float2(v); }
+
 __device__ __forceinline__ void st_c(double2* p, double2 v) { *p = v; }
 __device__ __forceinline__ void st_c(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void st_c(__half2* p, float2 v) { *p = __float22half2_rn(v); }
@@ -107,6 +111,7 @@ struct CgScalars {
 };
 constexpr int kFlagBreakdown = 1;
 constexpr int kFlagNaN = 2;
+constexpr int kFlagTimeout = 4;   // a bounded device-side wait gave up
 
 enum RedMode : int {
     RED_NONE = 0,
@@ -141,6 +146,7 @@ struct DslashArgs {
     int has_mu;                         // 1 if any factor differs from 1
     int t_only;                         // 1: temporal hops only (d D / d mu)
     int l2_prefetch;                    // 1: bulk-prefetch each tile's links into L2
+    int* status;                        // bounded waits that give up OR kFlagTimeout here (or null)
     double r12_inv_scale;               // 1 / s for R12 fat links
     int red_mode;
     int finish;
@@ -154,12 +160,15 @@ struct DslashArgs {
 enum Epi : int { EPI_NONE = 0, EPI_X = 1, EPI_XY = 2 };
 
 // Thread mapping and spinor layout of one launch: rpt rhs per thread,
-// compiled for at least minb resident 256-thread blocks per SM, with packed
-// f32x2 complex arithmetic when pack = 1 (FP32 arithmetic only).
+// compiled for at least minb resident 256-thread blocks per SM; kind 0 is
+// the register kernel, 1 the register kernel with packed f32x2 complex
+// arithmetic (FP32 arithmetic only), 2 the kernel with links staged in shared
+// memory by bulk copies (FP32 arithmetic only).
+enum DslashKind : int { KIND_REG = 0, KIND_PACKED = 1, KIND_STAGED = 2 };
 struct DslashTune {
     int rpt;
     int minb;
-    int pack;
+    int kind;
     int layout;     // HISQ_AOS or HISQ_SOA
     int prefetch;   // bulk L2 prefetch of each tile's links
 };
@@ -169,9 +178,11 @@ struct DslashTune {
 cudaError_t launch_dslash(const DslashArgs& a, int prec, int ru, int rn, int epi,
                           const DslashTune& t, cudaStream_t s);
 bool dslash_variant_supported(int prec, int ru, int rn, int epi);
-// Built (rpt, minb, pack) mappings of a precision, and the default one for an rpt.
-bool dslash_mapping_built(int prec, int rpt, int minb, int pack);
+// Built (rpt, minb, kind) mappings of a precision, and the default one for an rpt.
+bool dslash_mapping_built(int prec, int rpt, int minb, int kind);
 DslashTune dslash_default_tune(int prec, int rpt, int layout);
+// Whether the staged-link kernel can run this lattice with `groups` groups of rpt rhs.
+bool dslash_staged_ok(const Geom& g, int prec, int rpt, int groups);
 // Largest rhs-per-thread value instantiated for a precision.
 int dslash_max_rpt(int prec);
 

@@ -36,10 +36,11 @@ MAX_RHS = 16
 
 HISQ_OP_M, HISQ_OP_MDAG, HISQ_OP_DM_DMU = 0, 1, 2
 HISQ_OP_D2M_DMU2, HISQ_OP_D3M_DMU3, HISQ_OP_D4M_DMU4 = 3, 4, 5
-HISQ_MAP_PACKED, HISQ_MAP_L2_PREFETCH = 1, 2
+HISQ_MAP_PACKED, HISQ_MAP_L2_PREFETCH, HISQ_MAP_STAGED = 1, 2, 4
 
 EXPORTED = ["hisq_version", "hisq_last_error", "hisq_gauge_load", "hisq_gauge_free",
-            "hisq_gauge_info", "hisq_set_dslash_mapping", "hisq_link_compress",
+            "hisq_gauge_info", "hisq_set_dslash_mapping", "hisq_get_dslash_mapping",
+            "hisq_link_compress",
             "hisq_link_reconstruct", "hisq_dslash", "hisq_dslash_ex", "hisq_mdagm",
             "hisq_apply_m", "hisq_link_force", "hisq_cdot",
             "hisq_cg_default_params", "hisq_cg_solve"]
@@ -87,6 +88,7 @@ def library() -> ctypes.CDLL:
         "hisq_gauge_free": (c_int, [vp]),
         "hisq_gauge_info": (c_int, [vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_size_t)]),
         "hisq_set_dslash_mapping": (c_int, [vp, c_int, c_int, c_int]),
+        "hisq_get_dslash_mapping": (c_int, [vp, c_int, c_int, ip, ip, ip]),
         "hisq_link_compress": (c_int, [ip, vp, c_int, vp, ctypes.POINTER(c_double), vp]),
         "hisq_link_reconstruct": (c_int, [ip, vp, c_int, vp, vp]),
         "hisq_dslash": (c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int, c_int, vp]),
@@ -244,6 +246,14 @@ def hisq_set_dslash_mapping(g: Gauge, rhs_per_thread: int, min_blocks: int = 0,
     (packed f32x2 arithmetic, L2 link prefetch); 0 = automatic."""
     _check(library().hisq_set_dslash_mapping(g.handle, int(rhs_per_thread), int(min_blocks),
                                              int(flags)))
+
+
+def hisq_get_dslash_mapping(g: Gauge, n: int, prec: int) -> tuple:
+    """(rhs per thread, min blocks, HISQ_MAP_* flags) a Dslash of n rhs will use."""
+    r, b, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(library().hisq_get_dslash_mapping(g.handle, int(n), int(prec), ctypes.byref(r),
+                                             ctypes.byref(b), ctypes.byref(f)))
+    return r.value, b.value, f.value
 
 
 def hisq_link_compress(L, links, recon, packed, stream=None) -> float:

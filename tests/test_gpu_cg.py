@@ -143,7 +143,9 @@ def test_zero_source_and_eigenvector_source_in_one_bundle(gpu_lib):
         xg, st = solve(H, L, U, N, b, m, prec=prec, ru=18, rn=18)
         assert rel_l2(xg[0], ve / lam) < 1e-9
         assert np.all(xg[1] == 0) and st.iters[1] == 0
-        assert st.iters[0] <= 12 and st.iters[2] > st.iters[0]
+        # one CG step solves the eigenvector; it is confirmed at the next host
+        # poll (every 10 iterations), FP32 after one more reliable update
+        assert st.iters[0] <= (12 if prec == 0 else 30) and st.iters[2] > st.iters[0]
 
 
 def test_host_buffers_and_initial_guess(gpu_lib):

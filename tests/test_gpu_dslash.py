@@ -282,3 +282,61 @@ def test_every_built_mapping_matches_oracle(gpu_lib, rpt, minb):
                 assert rel_l2(got, ref[k]) < 1e-6
     finally:
         H.hisq_gauge_free(g)
+
+
+@pytest.mark.parametrize("L", [(16, 16, 4, 6), (32, 8, 6, 4)])
+@pytest.mark.parametrize("prec,ru,rn", [(1, 18, 14), (1, 12, 14), (1, 18, 18), (2, 18, 14), (2, 14, 14)])
+def test_staged_link_kernel_matches_oracle(gpu_lib, L, prec, ru, rn):
+    """Links staged in shared memory by bulk copies: every mapping, both layouts, mu."""
+    import torch
+    H = gpu_lib
+    U, N = links(L)
+    g = load(H, L, prec, ru, rn)
+    try:
+        for n, rpt, minb in ((8, 8, 2), (8, 8, 3), (8, 4, 2), (4, 4, 3), (4, 4, 2)):
+            H.hisq_set_dslash_mapping(g, rpt, minb, H.HISQ_MAP_STAGED)
+            assert H.hisq_get_dslash_mapping(g, n, prec) == (rpt, minb, H.HISQ_MAP_STAGED)
+            v = gen.gaussian_source(L, n, seed=70 + n)
+            for layout in (H.HISQ_AOS, H.HISQ_SOA):
+                for parity, mu in ((0, 0.0), (1, 0.0), (0, 0.2)):
+                    src = v if layout == H.HISQ_AOS else np.ascontiguousarray(np.swapaxes(v, 1, 2))
+                    vd = [to_dev(src[k], prec) for k in range(n)]
+                    wd = [torch.full_like(t, float("nan")) for t in vd]
+                    H.hisq_dslash_ex(g, mu, vd, wd, parity, prec, layout)
+                    torch.cuda.synchronize()
+                    ref = O.dslash_parity(U, N, v, L, parity, mu)
+                    for k in range(n):
+                        got = from_dev(wd[k])
+                        got = got if layout == H.HISQ_AOS else np.swapaxes(got, 0, 1)
+                        assert rel_l2(got, ref[k]) < TOL[prec], (n, rpt, minb, layout, parity, mu, k)
+    finally:
+        H.hisq_gauge_free(g)
+
+
+def test_staged_mapping_falls_back_where_the_tile_does_not_fit(gpu_lib):
+    H = gpu_lib
+    g = load(H, (8, 8, 8, 8), 1, 18, 14)      # an x-y plane holds 32 sites < one 128-site tile
+    try:
+        H.hisq_set_dslash_mapping(g, 8, 2, H.HISQ_MAP_STAGED)
+        assert H.hisq_get_dslash_mapping(g, 8, 1)[2] & H.HISQ_MAP_STAGED == 0
+    finally:
+        H.hisq_gauge_free(g)
+
+
+def test_staged_cg_solve_matches_oracle(gpu_lib):
+    import torch
+    H = gpu_lib
+    L, m = (16, 16, 4, 6), 0.05
+    U, N = links(L)
+    b = gen.z2_source(L, 8, seed=81)
+    g = load(H, L, 1, 18, 14)
+    try:
+        H.hisq_set_dslash_mapping(g, 8, 2, H.HISQ_MAP_STAGED)
+        bt = [torch.from_numpy(b[k]).cuda() for k in range(8)]
+        xt = [torch.zeros_like(t) for t in bt]
+        H.hisq_cg_solve(g, m, 0.0, bt, xt, 1e-10, H.cg_params(inner_prec=1))
+        x = np.stack([t.cpu().numpy() for t in xt])
+    finally:
+        H.hisq_gauge_free(g)
+    res = O.true_relative_residual(lambda q: O.apply_Ae(U, N, q, L, m), x, b)
+    assert np.all(res <= 1e-10)
