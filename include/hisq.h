@@ -237,6 +237,29 @@ hisq_status hisq_link_force(hisq_gauge g, double mu, int hop, const void* const 
 hisq_status hisq_cdot(hisq_gauge g, const void* const a[], const void* const b[], int n,
                       long long len, double* out, void* stream);
 
+/*
+ * hisq_cdot without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * processes whose device memory is entirely owned by another allocator (an
+ * extra allocation would fail or fragment its pool) and latency-critical
+ * code that cannot accept the device synchronisation cudaMalloc implies.
+ * Same operation, arguments and result as hisq_cdot, without a handle: the
+ * reduction scratch is a fixed device array of about 1 MiB inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits. n is limited to 16, the bundle size that array holds; larger n
+ * returns HISQ_EINVAL.
+ *   - The first call on a device looks up the array's device address there
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before starting any stream capture.
+ *   - Every call on a device shares the one array and leaves its last
+ *     contents there; each call clears the part that must start at zero.
+ *     Calls whose kernels overlap on the GPU (other streams, other host
+ *     threads) race on the array: serialise them.
+ * Synchronises `stream`.
+ */
+hisq_status hisq_cdot_noalloc(const void* const a[], const void* const b[], int n,
+                              long long len, double* out, void* stream);
+
 /* CG parameters; hisq_cg_default_params fills the defaults noted below. */
 typedef struct {
     int maxiter;           /* iteration cap (100000) */

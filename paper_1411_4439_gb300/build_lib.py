@@ -40,7 +40,7 @@ FAMILIES = [
     ("dslash_f16_12_14", dict(HISQ_STORE="__half", HISQ_RU=12, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
     ("dslash_f16_14_14", dict(HISQ_STORE="__half", HISQ_RU=14, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
 ]
-PLAIN = ["hisq_api", "dslash_dispatch", "gauge", "blas", "force"]
+PLAIN = ["hisq_api", "dslash_dispatch", "gauge", "blas", "force", "noalloc"]
 
 
 def _nvcc() -> str:

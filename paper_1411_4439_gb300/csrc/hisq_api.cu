@@ -90,6 +90,9 @@ bool is_device_pointer(const void* p) {
 }  // namespace
 
 namespace hisq {
+// Message for hisq_last_error() from entry points in other translation units.
+void record_error(const char* msg) { g_last_error = msg; }
+
 int device_sm_count() {
     static int cached[64] = {0};
     int dev = 0;

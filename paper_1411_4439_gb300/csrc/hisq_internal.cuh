@@ -260,5 +260,6 @@ cudaError_t launch_cdot(const ForcePtrs& vw, long long len, int n, RedScratch re
                         cudaStream_t s);
 
 int device_sm_count();
+void record_error(const char* msg);
 
 }  // namespace hisq

@@ -42,7 +42,7 @@ EXPORTED = ["hisq_version", "hisq_last_error", "hisq_gauge_load", "hisq_gauge_fr
             "hisq_gauge_info", "hisq_set_dslash_mapping", "hisq_get_dslash_mapping",
             "hisq_link_compress",
             "hisq_link_reconstruct", "hisq_dslash", "hisq_dslash_ex", "hisq_mdagm",
-            "hisq_apply_m", "hisq_link_force", "hisq_cdot",
+            "hisq_apply_m", "hisq_link_force", "hisq_cdot", "hisq_cdot_noalloc",
             "hisq_cg_default_params", "hisq_cg_solve"]
 
 
@@ -101,6 +101,8 @@ def library() -> ctypes.CDLL:
                                     c_double, vp, vp]),
         "hisq_cdot": (c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, ctypes.c_longlong,
                               ctypes.POINTER(c_double), vp]),
+        "hisq_cdot_noalloc": (c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, ctypes.c_longlong,
+                                      ctypes.POINTER(c_double), vp]),
         "hisq_cg_default_params": (None, [ctypes.POINTER(hisq_cg_params)]),
         "hisq_cg_solve": (c_int, [vp, c_double, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
                                   c_double, ctypes.POINTER(hisq_cg_params),
@@ -319,6 +321,22 @@ def hisq_cdot(g: Gauge, a, b, stream=None) -> np.ndarray:
     out = (ctypes.c_double * (2 * n))()
     _check(library().hisq_cdot(g.handle, _ptr_array(a), _ptr_array(b), n, length, out,
                                _stream_handle(stream, *a)))
+    arr = np.frombuffer(out, dtype=np.float64).copy()
+    return arr[0::2] + 1j * arr[1::2]
+
+
+def hisq_cdot_noalloc(a, b, stream=None) -> np.ndarray:
+    """<a_k, b_k> like hisq_cdot, with no device allocation (static library scratch)."""
+    if len(a) != len(b):
+        raise ValueError("a and b need the same number of rhs")
+    n = len(a)
+    length = int(a[0].numel()) // (2 if str(a[0].dtype).endswith("float64") else 1)
+    for t in list(a) + list(b):
+        if t.numel() != a[0].numel():
+            raise ValueError("all vectors need the same length")
+    out = (ctypes.c_double * (2 * max(n, 1)))()
+    _check(library().hisq_cdot_noalloc(_ptr_array(a), _ptr_array(b), n, length, out,
+                                       _stream_handle(stream, *a)))
     arr = np.frombuffer(out, dtype=np.float64).copy()
     return arr[0::2] + 1j * arr[1::2]
 
