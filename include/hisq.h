@@ -132,10 +132,19 @@ hisq_status hisq_gauge_info(hisq_gauge g, int L[4], hisq_prec* prec,
  * HISQ_MAP_L2_PREFETCH to bulk-prefetch each tile's links into L2,
  * HISQ_MAP_STAGED to stage each tile's links in shared memory with bulk
  * asynchronous copies (FP32/FP16 storage; tiles of 128 sites made of whole
- * x-rows inside one y-z plane, at most 2 rhs groups). Mappings that are not
+ * x-rows inside one y-z plane, at most 2 rhs groups), HISQ_MAP_PIPELINED /
+ * HISQ_MAP_PIPELINED2 to keep the link and neighbour loads of the next one /
+ * two hops in flight while the current hop is multiplied (FP32/FP16). At
+ * most one of PACKED, STAGED, PIPELINED, PIPELINED2. Mappings that are not
  * built or do not fit n or the lattice fall back to the automatic choice.
  */
-enum { HISQ_MAP_PACKED = 1, HISQ_MAP_L2_PREFETCH = 2, HISQ_MAP_STAGED = 4 };
+enum {
+    HISQ_MAP_PACKED = 1,
+    HISQ_MAP_L2_PREFETCH = 2,
+    HISQ_MAP_STAGED = 4,
+    HISQ_MAP_PIPELINED = 8,
+    HISQ_MAP_PIPELINED2 = 16
+};
 hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_blocks,
                                     int flags);
 
@@ -143,6 +152,18 @@ hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_bl
  * rhs per thread, min blocks per SM and HISQ_MAP_* flags (host pointers). */
 hisq_status hisq_get_dslash_mapping(hisq_gauge g, int n, hisq_prec spinor_prec,
                                     int* rhs_per_thread, int* min_blocks, int* flags);
+
+/*
+ * Autotuner: times `reps` Dslash launches of every built mapping that fits
+ * n rhs, `spinor_prec` and `layout` on this handle (register and shared-
+ * memory-staged kernels, every register budget) and keeps the fastest for
+ * later calls of that shape (hisq_set_dslash_mapping still takes priority).
+ * Returns the choice and its time per launch (any output may be NULL).
+ * Allocates and frees scratch spinors; synchronises the device.
+ */
+hisq_status hisq_autotune_dslash(hisq_gauge g, int n, hisq_prec spinor_prec,
+                                 hisq_layout layout, int reps, int* rhs_per_thread,
+                                 int* min_blocks, int* flags, double* seconds);
 
 /*
  * Compress a canonical link field to `r` reals per link (R18/R14/R12, same
@@ -308,6 +329,30 @@ hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu,
                           const void* const b[], void* const x[], int n,
                           double tol, const hisq_cg_params* p,
                           hisq_cg_stats* stats, void* stream);
+
+/*
+ * Several independent solves advanced together, e.g. bundles on gauge fields
+ * of uneven volume: each chunk of iterations of all unfinished solves is one
+ * CUDA graph whose branches run the solves concurrently, so small lattices
+ * share the GPU instead of running one after another. Every problem has its
+ * own handle (distinct handles required), mass, mu, bundle, size and
+ * tolerance, with the meaning of hisq_cg_solve; the parameters p are shared.
+ * stats (may be NULL) receives one entry per problem. Returns HISQ_OK when
+ * every problem converged, else the first failing problem's status.
+ */
+typedef struct {
+    hisq_gauge g;
+    double mass;
+    double mu;
+    const void* const* b;
+    void* const* x;
+    int n;
+    double tol;
+} hisq_cg_problem;
+
+hisq_status hisq_cg_solve_batched(const hisq_cg_problem* problems, int nprob,
+                                  const hisq_cg_params* p, hisq_cg_stats* stats,
+                                  void* stream);
 
 #ifdef __cplusplus
 }

@@ -85,10 +85,12 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         obj = os.path.join(BUILD, name + ".o")
         tasks.append(([nvcc, *ARCH, *NVFLAGS, "-c", os.path.join(CSRC, name + ".cu"), "-o", obj], obj))
     for name, defs in FAMILIES:
-        obj = os.path.join(BUILD, name + ".o")
-        dflags = [f"-D{k}={v}" for k, v in defs.items()] + [f"-DHISQ_FAMILY={name}"]
-        tasks.append(([nvcc, *ARCH, *NVFLAGS, *dflags, "-c", os.path.join(CSRC, "dslash_inst.cu"),
-                       "-o", obj], obj))
+        for layout, suffix in ((0, "aos"), (1, "soa")):
+            obj = os.path.join(BUILD, f"{name}_{suffix}.o")
+            dflags = [f"-D{k}={v}" for k, v in defs.items()]
+            dflags += [f"-DHISQ_FAMILY={name}_{suffix}", f"-DHISQ_LAYOUT={layout}"]
+            tasks.append(([nvcc, *ARCH, *NVFLAGS, *dflags, "-c", os.path.join(CSRC, "dslash_inst.cu"),
+                           "-o", obj], obj))
     jobs = jobs or min(len(tasks), max(1, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(_compile, tasks))

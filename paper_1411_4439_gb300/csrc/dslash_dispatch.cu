@@ -5,8 +5,14 @@
 
 namespace hisq {
 
-#define HISQ_FAMILY_DECL(name) \
-    cudaError_t name(const DslashArgs&, int epi, int rpt, int minb, int kind, int layout, cudaStream_t)
+#define HISQ_FAMILY_DECL(name)                                                                     \
+    cudaError_t name##_aos(const DslashArgs&, int epi, int rpt, int minb, int kind, cudaStream_t); \
+    cudaError_t name##_soa(const DslashArgs&, int epi, int rpt, int minb, int kind, cudaStream_t);   \
+    static cudaError_t name(const DslashArgs& a, int epi, int rpt, int minb, int kind, int layout,  \
+                            cudaStream_t s) {                                                       \
+        return layout == HISQ_SOA ? name##_soa(a, epi, rpt, minb, kind, s)                          \
+                                  : name##_aos(a, epi, rpt, minb, kind, s);                         \
+    }
 HISQ_FAMILY_DECL(dslash_f64_18_18);
 HISQ_FAMILY_DECL(dslash_f32_18_18);
 HISQ_FAMILY_DECL(dslash_f32_18_14);
@@ -27,6 +33,7 @@ bool dslash_mapping_built(int prec, int rpt, int minb, int kind) {
     switch (key) {
         case 140: case 230: case 231: case 420: case 421: case 430: case 820: case 821:
         case 422: case 432: case 822: case 832:
+        case 423: case 414: case 424: case 813:
             return true;
         default:
             return false;
@@ -72,6 +79,11 @@ cudaError_t launch_dslash(const DslashArgs& a, int prec, int ru, int rn, int epi
                           const DslashTune& t, cudaStream_t s) {
     if (!dslash_variant_supported(prec, ru, rn, epi)) return cudaErrorInvalidValue;
     if (!dslash_mapping_built(prec, t.rpt, t.minb, t.kind)) return cudaErrorInvalidValue;
+    if (a.t_only && (t.kind == KIND_PIPE1 || t.kind == KIND_PIPE2)) {
+        // the pipelined kernels run all 16 hops; temporal-only operators take
+        // the register kernel of the same rhs count
+        return launch_dslash(a, prec, ru, rn, epi, dslash_default_tune(prec, t.rpt, t.layout), s);
+    }
     if (t.prefetch != a.l2_prefetch) {
         DslashArgs c = a;
         c.l2_prefetch = t.prefetch;

@@ -3,15 +3,19 @@
 // This file is compiled once per family with
 //   -DHISQ_STORE=<double|float|__half> -DHISQ_RU=<18|12|14> -DHISQ_RN=<18|14>
 //   -DHISQ_FAMILY=<function name> -DHISQ_MAX_RPT=<4|8> -DHISQ_WITH_XY=<0|1>
+//   -DHISQ_LAYOUT=<0 (AoS)|1 (SoA)>
 // so the families build in parallel translation units. Each family holds the
 // thread mappings (rhs per thread, minimum resident blocks, kernel kind)
-// listed in dslash_dispatch.cu, for both spinor layouts. Kinds: 0 register
+// listed in dslash_dispatch.cu, for one spinor layout. Kinds: 0 register
 // kernel, 1 register kernel with packed f32x2 arithmetic, 2 links staged in
-// shared memory by bulk copies.
+// shared memory by bulk copies, 3 and 4 register kernel with the loads of
+// the next one or two hops in flight (software pipeline).
+#include "dslash_pipe.cuh"
 #include "dslash_staged.cuh"
 
-#if !defined(HISQ_STORE) || !defined(HISQ_RU) || !defined(HISQ_RN) || !defined(HISQ_FAMILY)
-#error "dslash_inst.cu needs HISQ_STORE, HISQ_RU, HISQ_RN and HISQ_FAMILY"
+#if !defined(HISQ_STORE) || !defined(HISQ_RU) || !defined(HISQ_RN) || !defined(HISQ_FAMILY) || \
+    !defined(HISQ_LAYOUT)
+#error "dslash_inst.cu needs HISQ_STORE, HISQ_RU, HISQ_RN, HISQ_FAMILY and HISQ_LAYOUT"
 #endif
 
 namespace hisq {
@@ -19,6 +23,7 @@ namespace hisq {
 #define HISQ_INST(R, B, P) \
     launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, R, B, EPI, LAYOUT, P>(a, s)
 #define HISQ_STAGED(R, B) launch_dslash_staged<S, S, HISQ_RU, HISQ_RN, R, B, EPI, LAYOUT>(a, s)
+#define HISQ_PIPE(R, B, D) launch_dslash_pipe<S, S, HISQ_RU, HISQ_RN, R, B, D, EPI, LAYOUT>(a, s)
 
 template <int EPI, int LAYOUT>
 static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, int kind,
@@ -40,6 +45,10 @@ static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, int
         case 432: return HISQ_STAGED(4, 3);
         case 822: return HISQ_STAGED(8, 2);
         case 832: return HISQ_STAGED(8, 3);
+        case 423: return HISQ_PIPE(4, 2, 1);
+        case 414: return HISQ_PIPE(4, 1, 2);
+        case 424: return HISQ_PIPE(4, 2, 2);
+        case 813: return HISQ_PIPE(8, 1, 1);
 #else
         // FP64 storage and arithmetic
         case 120: return HISQ_INST(1, 2, false);
@@ -52,6 +61,7 @@ static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, int
 
 #undef HISQ_INST
 #undef HISQ_STAGED
+#undef HISQ_PIPE
 
 template <int LAYOUT>
 static cudaError_t family_by_epi(const DslashArgs& a, int epi, int rpt, int minb, int kind,
@@ -66,10 +76,9 @@ static cudaError_t family_by_epi(const DslashArgs& a, int epi, int rpt, int minb
     }
 }
 
-cudaError_t HISQ_FAMILY(const DslashArgs& a, int epi, int rpt, int minb, int kind, int layout,
-                        cudaStream_t s) {
-    return layout == HISQ_SOA ? family_by_epi<HISQ_SOA>(a, epi, rpt, minb, kind, s)
-                              : family_by_epi<HISQ_AOS>(a, epi, rpt, minb, kind, s);
+// One translation unit per (family, spinor layout): HISQ_LAYOUT selects it.
+cudaError_t HISQ_FAMILY(const DslashArgs& a, int epi, int rpt, int minb, int kind, cudaStream_t s) {
+    return family_by_epi<HISQ_LAYOUT>(a, epi, rpt, minb, kind, s);
 }
 
 }  // namespace hisq

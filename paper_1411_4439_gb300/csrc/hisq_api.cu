@@ -9,6 +9,7 @@
 // reliable updates (every `reliable_every` iterations, or when a residual
 // fell by `reliable_delta`, or when an iterated residual claims
 // convergence), and replays the iterations from a captured CUDA graph.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -170,6 +171,7 @@ struct hisq_gauge_s {
     int tune_rpt = 0;            // 0 = automatic
     int tune_minb = 0;
     int tune_flags = 0;          // HISQ_MAP_* bits
+    std::map<int, DslashTune> tuned;   // autotuned mappings by tuned_key(n, prec, layout)
     void* mdagm_tmp = nullptr;
     size_t mdagm_tmp_bytes = 0;
     double* dot_partials = nullptr;     // reduction scratch of hisq_cdot
@@ -333,8 +335,12 @@ extern "C" hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rpt, int minb, 
     if (rpt != 0 && rpt != 1 && rpt != 2 && rpt != 4 && rpt != 8)
         return fail(HISQ_EINVAL, "rhs per thread must be 0 (auto), 1, 2, 4 or 8");
     if (minb < 0 || minb > 8) return fail(HISQ_EINVAL, "min blocks per SM must be 0 (auto) .. 8");
-    if (flags & ~(HISQ_MAP_PACKED | HISQ_MAP_L2_PREFETCH | HISQ_MAP_STAGED))
+    if (flags & ~(HISQ_MAP_PACKED | HISQ_MAP_L2_PREFETCH | HISQ_MAP_STAGED | HISQ_MAP_PIPELINED |
+                  HISQ_MAP_PIPELINED2))
         return fail(HISQ_EINVAL, "unknown mapping flags %d", flags);
+    const int kinds = !!(flags & HISQ_MAP_PACKED) + !!(flags & HISQ_MAP_STAGED) +
+                      !!(flags & HISQ_MAP_PIPELINED) + !!(flags & HISQ_MAP_PIPELINED2);
+    if (kinds > 1) return fail(HISQ_EINVAL, "mapping flags %d name more than one kernel kind", flags);
     g->tune_rpt = rpt;
     g->tune_minb = minb;
     g->tune_flags = flags;
@@ -417,15 +423,37 @@ int auto_rpt(int n, int prec) {
     return r;
 }
 
-// Thread mapping for n rhs: the requested rpt, else the handle's setting,
-// else the largest power of two dividing n (at most 8 rhs groups per block).
+int tuned_key(int n, int prec, int layout) { return n * 100 + prec * 10 + layout; }
+
+int kind_of_flags(int flags) {
+    if (flags & HISQ_MAP_PACKED) return KIND_PACKED;
+    if (flags & HISQ_MAP_STAGED) return KIND_STAGED;
+    if (flags & HISQ_MAP_PIPELINED) return KIND_PIPE1;
+    if (flags & HISQ_MAP_PIPELINED2) return KIND_PIPE2;
+    return KIND_REG;
+}
+
+int flags_of_tune(const DslashTune& t) {
+    const int k = t.kind == KIND_PACKED   ? HISQ_MAP_PACKED
+                  : t.kind == KIND_STAGED ? HISQ_MAP_STAGED
+                  : t.kind == KIND_PIPE1  ? HISQ_MAP_PIPELINED
+                  : t.kind == KIND_PIPE2  ? HISQ_MAP_PIPELINED2
+                                          : 0;
+    return k | (t.prefetch ? HISQ_MAP_L2_PREFETCH : 0);
+}
+
+// Thread mapping for n rhs: the requested rpt, else the handle's explicit
+// setting, else the autotuned mapping for (n, prec, layout), else the
+// largest power of two dividing n (at most 8 rhs groups per block).
 DslashTune pick_tune(hisq_gauge g, int n, int prec, int requested, int layout) {
+    if (!requested && g->tune_rpt == 0 && g->tune_flags == 0) {
+        auto it = g->tuned.find(tuned_key(n, prec, layout));
+        if (it != g->tuned.end()) return it->second;
+    }
     int r = requested ? requested : g->tune_rpt;
     if (r == 0 || r > dslash_max_rpt(prec) || n % r != 0 || n / r > 8) r = auto_rpt(n, prec);
     DslashTune t = dslash_default_tune(prec, r, layout);
-    int kind = KIND_REG;
-    if (g->tune_flags & HISQ_MAP_PACKED) kind = KIND_PACKED;
-    if (g->tune_flags & HISQ_MAP_STAGED) kind = KIND_STAGED;
+    const int kind = kind_of_flags(g->tune_flags);
     if (!requested && g->tune_minb && r == g->tune_rpt && dslash_mapping_built(prec, r, g->tune_minb, kind) &&
         (kind != KIND_STAGED || dslash_staged_ok(g->g, prec, r, n / r))) {
         t.minb = g->tune_minb;
@@ -445,9 +473,7 @@ extern "C" hisq_status hisq_get_dslash_mapping(hisq_gauge g, int n, hisq_prec pr
     const DslashTune t = pick_tune(g, n, prec, 0, HISQ_AOS);
     if (rpt) *rpt = t.rpt;
     if (minb) *minb = t.minb;
-    if (flags)
-        *flags = (t.kind == KIND_PACKED ? HISQ_MAP_PACKED : 0) | (t.kind == KIND_STAGED ? HISQ_MAP_STAGED : 0) |
-                 (t.prefetch ? HISQ_MAP_L2_PREFETCH : 0);
+    if (flags) *flags = flags_of_tune(t);
     return HISQ_OK;
 }
 
@@ -563,6 +589,98 @@ extern "C" hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v
         b.x[k] = v[k];
     }
     HISQ_CUDA(launch_dslash(b, spinor_prec, ru, rn, EPI_X, t, s));
+    return HISQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times every built Dslash mapping that fits (n, prec, layout) on
+// this handle and keeps the fastest for later calls of that shape.
+// ---------------------------------------------------------------------------
+namespace {
+
+std::vector<DslashTune> candidate_tunes(hisq_gauge g, int n, int prec, int layout) {
+    std::vector<DslashTune> out;
+    const int rpts[] = {1, 2, 4, 8};
+    const int minbs[] = {1, 2, 3, 4};
+    const int kinds[] = {KIND_REG, KIND_PACKED, KIND_STAGED, KIND_PIPE1, KIND_PIPE2};
+    for (int r : rpts) {
+        if (r > dslash_max_rpt(prec) || n % r != 0 || n / r > 8) continue;
+        for (int b : minbs)
+            for (int k : kinds) {
+                if (!dslash_mapping_built(prec, r, b, k)) continue;
+                if (k == KIND_STAGED && !dslash_staged_ok(g->g, prec, r, n / r)) continue;
+                DslashTune t = dslash_default_tune(prec, r, layout);
+                t.minb = b;
+                t.kind = k;
+                out.push_back(t);
+            }
+    }
+    return out;
+}
+
+}  // namespace
+
+extern "C" hisq_status hisq_autotune_dslash(hisq_gauge g, int n, hisq_prec prec, hisq_layout layout, int reps,
+                                           int* rpt, int* minb, int* flags, double* seconds) {
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
+    if (!valid_prec(prec) || (prec != HISQ_F64 && prec != g->prec))
+        return fail(HISQ_EINVAL, "precision %d not available on this handle", prec);
+    if (layout != HISQ_AOS && layout != HISQ_SOA) return fail(HISQ_EINVAL, "unknown layout %d", layout);
+    if (reps < 1) reps = 5;
+    std::lock_guard<std::mutex> lock(g->mtx);
+    const size_t per = (size_t)g->g.vh * 3 * prec_complex_bytes(prec);
+    void* buf = nullptr;
+    HISQ_CUDA(cudaMalloc(&buf, 2 * per * n));
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+        cudaFree(buf);
+    };
+    cudaError_t e = cudaMemset(buf, 0, 2 * per * n);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        HISQ_CUDA(e);
+    }
+    DslashArgs a;
+    fill_common(a, g, prec, 0, n);
+    for (int k = 0; k < n; ++k) {
+        a.in[k] = (char*)buf + per * k;
+        a.out[k] = (char*)buf + per * (n + k);
+    }
+    const int ru = link_recon_u(g, prec), rn = link_recon_n(g, prec);
+    double best = HUGE_VAL;
+    DslashTune best_t = dslash_default_tune(prec, auto_rpt(n, prec), layout);
+    for (const DslashTune& t : candidate_tunes(g, n, prec, layout)) {
+        e = launch_dslash(a, prec, ru, rn, EPI_NONE, t, s);   // warm-up (and first-use set-up)
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch_dslash(a, prec, ru, rn, EPI_NONE, t, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cleanup();
+            HISQ_CUDA(e);
+        }
+        const double sec = ms * 1e-3 / reps;
+        if (sec < best) {
+            best = sec;
+            best_t = t;
+        }
+    }
+    cleanup();
+    g->tuned[tuned_key(n, prec, layout)] = best_t;
+    if (rpt) *rpt = best_t.rpt;
+    if (minb) *minb = best_t.minb;
+    if (flags) *flags = flags_of_tune(best_t);
+    if (seconds) *seconds = best;
     return HISQ_OK;
 }
 
@@ -958,113 +1076,143 @@ struct Solver {
 
 }  // namespace
 
-extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const void* const b[],
-                                     void* const x[], int n, double tol, const hisq_cg_params* p,
-                                     hisq_cg_stats* stats, void* stream) {
-    const auto t0 = std::chrono::steady_clock::now();
-    if (!g) return fail(HISQ_EINVAL, "NULL handle");
-    if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
-    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(HISQ_EINVAL, "tol must be positive and finite");
-    if (!std::isfinite(mass) || !std::isfinite(mu)) return fail(HISQ_EINVAL, "mass and mu must be finite");
-    if (!b || !x) return fail(HISQ_EINVAL, "NULL pointer array");
-    for (int k = 0; k < n; ++k)
-        if (!b[k] || !x[k]) return fail(HISQ_EINVAL, "NULL source or solution pointer for rhs %d", k);
-    hisq_cg_params prm;
-    hisq_cg_default_params(&prm);
-    if (p) prm = *p;
-    if (!valid_prec(prm.inner_prec)) return fail(HISQ_EINVAL, "unknown inner precision %d", prm.inner_prec);
-    if (prm.inner_prec != HISQ_F64 && prm.inner_prec != g->prec)
-        return fail(HISQ_EINVAL, "inner precision %d needs links stored in that precision (handle has %d)",
-                    prm.inner_prec, g->prec);
-    if (prm.even_odd && mu != 0.0)
-        return fail(HISQ_EINVAL, "mu != 0 needs the full-lattice solve (even_odd = 0)");
-    if (prm.maxiter < 1) return fail(HISQ_EINVAL, "maxiter must be >= 1");
-    if (prm.check_every < 1) prm.check_every = 1;
-    if (prm.reliable_every < 1) prm.reliable_every = 1 << 30;
-    if (prm.spinor_layout != HISQ_AOS && prm.spinor_layout != HISQ_SOA)
-        return fail(HISQ_EINVAL, "unknown spinor layout %d", prm.spinor_layout);
-    if (!(prm.reliable_delta >= 0.0 && prm.reliable_delta < 1.0))
-        return fail(HISQ_EINVAL, "reliable_delta must be in [0, 1)");
+// One solve in progress: setup, host-side decisions after every chunk of
+// iterations, and the final copy-out. hisq_cg_solve drives one of these;
+// hisq_cg_solve_batched drives several through one CUDA graph per chunk.
+namespace {
 
-    std::lock_guard<std::mutex> lock(g->mtx);
-    cudaStream_t s = (cudaStream_t)stream;
-    const int full = prm.even_odd ? 0 : 1;
+struct CgRun {
+    hisq_gauge g = nullptr;
     Workspace* w = nullptr;
-    hisq_status st = get_workspace(g, n, prm.inner_prec, full, &w);
-    if (st != HISQ_OK) return st;
-
     Solver sv;
-    sv.g = g;
-    sv.w = w;
-    sv.n = n;
-    sv.prec = prm.inner_prec;
-    sv.full = full;
-    sv.tune = pick_tune(g, n, sv.prec, prm.rhs_per_thread, prm.spinor_layout);
-    sv.tune64 = pick_tune(g, n, HISQ_F64, 0, prm.spinor_layout);
-    sv.mass = mass;
-    sv.mu = mu;
-    sv.tol2 = tol * tol;
-
-    // sources and initial guess into the FP64 blocks
-    const size_t vec_bytes = (size_t)w->len * sizeof(double2);
-    const bool soa = prm.spinor_layout == HISQ_SOA;
-    const int halves = full ? 2 : 1;
-    // the caller's vectors are AoS; an SoA solve transposes them through r_hi
-    double2* bdst = soa ? w->r_hi : w->b_hi;
-    for (int k = 0; k < n; ++k)
-        HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(bdst, k), b[k], vec_bytes, cudaMemcpyDefault, s));
-    if (soa) HISQ_CUDA(launch_transpose_spinor(w->r_hi, w->b_hi, n, halves, g->g.vh, 1, s));
-    if (prm.use_x0) {
-        double2* xdst = soa ? w->r_hi : w->x_hi;
-        for (int k = 0; k < n; ++k)
-            HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(xdst, k), x[k], vec_bytes, cudaMemcpyDefault, s));
-        if (soa) HISQ_CUDA(launch_transpose_spinor(w->r_hi, w->x_hi, n, halves, g->g.vh, 1, s));
-    } else {
-        HISQ_CUDA(cudaMemsetAsync(w->x_hi, 0, vec_bytes * n, s));
-    }
-    HISQ_CUDA(cudaMemsetAsync(w->cg, 0, sizeof(CgScalars), s));
-    HISQ_CUDA(cudaMemsetAsync(w->x_lo, 0, (size_t)n * w->len * prec_complex_bytes(solution_prec(sv.prec)), s));
-    HISQ_CUDA(launch_norm_bb(sv.blas(), w->b_hi, s));
-    if (prm.use_x0) {
-        HISQ_CUDA(sv.true_residual(s));
-    } else {
-        HISQ_CUDA(launch_copy_residual(sv.blas(), w->b_hi, w->r_hi, sv.tol2, s));
-    }
-    HISQ_CUDA(launch_reliable_rescale(sv.blas(), sv.prec, w->r_hi, w->r_lo, w->p_lo, 1, s));
-    HISQ_CUDA(sv.poll(s));
-
-    // HISQ_DEBUG_CG=1 prints the device CG scalars at every host poll (stderr)
-    static const bool debug = [] {
-        const char* e = getenv("HISQ_DEBUG_CG");
-        return e != nullptr && e[0] != '\0' && e[0] != '0';
-    }();
+    hisq_cg_params prm;
+    void* const* x = nullptr;
+    int n = 0, halves = 1;
+    bool soa = true;
+    size_t vec_bytes = 0;
     int iters_k[kMaxRhs], seen_restarts[kMaxRhs], bad_updates[kMaxRhs];
-    for (int k = 0; k < n; ++k) iters_k[k] = seen_restarts[k] = bad_updates[k] = 0;
     int iter = 0, since_rel = 0, reliable = 0;
     hisq_status result = HISQ_OK;
-    const double d2 = prm.reliable_delta * prm.reliable_delta;
-    auto any_active = [&]() {
+    bool stop = false;
+    std::chrono::steady_clock::time_point t0;
+
+    static bool debug() {
+        static const bool d = [] {
+            const char* e = getenv("HISQ_DEBUG_CG");
+            return e != nullptr && e[0] != '\0' && e[0] != '0';
+        }();
+        return d;
+    }
+
+    // Validates the request (handle lock held by the caller).
+    static hisq_status check(hisq_gauge g, double mass, double mu, const void* const b[], void* const x[],
+                             int n, double tol, const hisq_cg_params* p, hisq_cg_params* out) {
+        if (!g) return fail(HISQ_EINVAL, "NULL handle");
+        if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
+        if (!(tol > 0.0) || !std::isfinite(tol)) return fail(HISQ_EINVAL, "tol must be positive and finite");
+        if (!std::isfinite(mass) || !std::isfinite(mu)) return fail(HISQ_EINVAL, "mass and mu must be finite");
+        if (!b || !x) return fail(HISQ_EINVAL, "NULL pointer array");
         for (int k = 0; k < n; ++k)
-            if (w->cg_host->active[k]) return true;
-        return false;
-    };
-    while (any_active()) {
-        if (w->cg_host->flags) break;
-        if (iter >= prm.maxiter) {
-            result = HISQ_ENOCONV;
-            break;
+            if (!b[k] || !x[k]) return fail(HISQ_EINVAL, "NULL source or solution pointer for rhs %d", k);
+        hisq_cg_params prm;
+        hisq_cg_default_params(&prm);
+        if (p) prm = *p;
+        if (!valid_prec(prm.inner_prec)) return fail(HISQ_EINVAL, "unknown inner precision %d", prm.inner_prec);
+        if (prm.inner_prec != HISQ_F64 && prm.inner_prec != g->prec)
+            return fail(HISQ_EINVAL, "inner precision %d needs links stored in that precision (handle has %d)",
+                        prm.inner_prec, g->prec);
+        if (prm.even_odd && mu != 0.0)
+            return fail(HISQ_EINVAL, "mu != 0 needs the full-lattice solve (even_odd = 0)");
+        if (prm.maxiter < 1) return fail(HISQ_EINVAL, "maxiter must be >= 1");
+        if (prm.check_every < 1) prm.check_every = 1;
+        if (prm.reliable_every < 1) prm.reliable_every = 1 << 30;
+        if (prm.spinor_layout != HISQ_AOS && prm.spinor_layout != HISQ_SOA)
+            return fail(HISQ_EINVAL, "unknown spinor layout %d", prm.spinor_layout);
+        if (!(prm.reliable_delta >= 0.0 && prm.reliable_delta < 1.0))
+            return fail(HISQ_EINVAL, "reliable_delta must be in [0, 1)");
+        *out = prm;
+        return HISQ_OK;
+    }
+
+    hisq_status start(hisq_gauge gg, double mass, double mu, const void* const b[], void* const xx[], int nn,
+                      double tol, const hisq_cg_params& p, cudaStream_t s) {
+        t0 = std::chrono::steady_clock::now();
+        g = gg;
+        prm = p;
+        x = xx;
+        n = nn;
+        const int full = prm.even_odd ? 0 : 1;
+        hisq_status st = get_workspace(g, n, prm.inner_prec, full, &w);
+        if (st != HISQ_OK) return st;
+        sv.g = g;
+        sv.w = w;
+        sv.n = n;
+        sv.prec = prm.inner_prec;
+        sv.full = full;
+        sv.tune = pick_tune(g, n, sv.prec, prm.rhs_per_thread, prm.spinor_layout);
+        sv.tune64 = pick_tune(g, n, HISQ_F64, 0, prm.spinor_layout);
+        sv.mass = mass;
+        sv.mu = mu;
+        sv.tol2 = tol * tol;
+        for (int k = 0; k < n; ++k) iters_k[k] = seen_restarts[k] = bad_updates[k] = 0;
+
+        // sources and initial guess into the FP64 blocks; the caller's vectors
+        // are AoS, an SoA solve transposes them through r_hi
+        vec_bytes = (size_t)w->len * sizeof(double2);
+        soa = prm.spinor_layout == HISQ_SOA;
+        halves = full ? 2 : 1;
+        double2* bdst = soa ? w->r_hi : w->b_hi;
+        for (int k = 0; k < n; ++k)
+            HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(bdst, k), b[k], vec_bytes, cudaMemcpyDefault, s));
+        if (soa) HISQ_CUDA(launch_transpose_spinor(w->r_hi, w->b_hi, n, halves, g->g.vh, 1, s));
+        if (prm.use_x0) {
+            double2* xdst = soa ? w->r_hi : w->x_hi;
+            for (int k = 0; k < n; ++k)
+                HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(xdst, k), x[k], vec_bytes, cudaMemcpyDefault, s));
+            if (soa) HISQ_CUDA(launch_transpose_spinor(w->r_hi, w->x_hi, n, halves, g->g.vh, 1, s));
+        } else {
+            HISQ_CUDA(cudaMemsetAsync(w->x_hi, 0, vec_bytes * n, s));
         }
+        HISQ_CUDA(cudaMemsetAsync(w->cg, 0, sizeof(CgScalars), s));
+        HISQ_CUDA(cudaMemsetAsync(w->x_lo, 0, (size_t)n * w->len * prec_complex_bytes(solution_prec(sv.prec)), s));
+        HISQ_CUDA(launch_norm_bb(sv.blas(), w->b_hi, s));
+        if (prm.use_x0) {
+            HISQ_CUDA(sv.true_residual(s));
+        } else {
+            HISQ_CUDA(launch_copy_residual(sv.blas(), w->b_hi, w->r_hi, sv.tol2, s));
+        }
+        HISQ_CUDA(launch_reliable_rescale(sv.blas(), sv.prec, w->r_hi, w->r_lo, w->p_lo, 1, s));
+        HISQ_CUDA(sv.poll(s));
+        update_stop();
+        return HISQ_OK;
+    }
+
+    void update_stop() {
+        const CgScalars& h = *w->cg_host;
+        bool any = false;
+        for (int k = 0; k < n; ++k) any = any || h.active[k];
+        if (!any || h.flags || result != HISQ_OK) stop = true;
+        if (!stop && iter >= prm.maxiter) {
+            result = HISQ_ENOCONV;
+            stop = true;
+        }
+    }
+
+    // Iterations to run before the next host decision.
+    int next_chunk() const {
         int chunk = prm.check_every;
         if (chunk > prm.reliable_every - since_rel) chunk = prm.reliable_every - since_rel;
         if (chunk > prm.maxiter - iter) chunk = prm.maxiter - iter;
-        if (chunk < 1) chunk = 1;
-        st = sv.run_chunk(chunk, prm.use_graphs != 0, s);
-        if (st != HISQ_OK) return st;
+        return chunk < 1 ? 1 : chunk;
+    }
+
+    // After `chunk` iterations ran on stream s: poll, decide on a reliable update.
+    hisq_status after_chunk(int chunk, cudaStream_t s) {
         iter += chunk;
         since_rel += chunk;
         HISQ_CUDA(sv.poll(s));
         const CgScalars& h = *w->cg_host;
-        if (debug) {
+        if (debug()) {
             fprintf(stderr, "[hisq cg] iter %d flags %d\n", iter, h.flags);
             for (int k = 0; k < n; ++k)
                 fprintf(stderr, "  rhs %d active %d frozen %d restarts %d rr %.3e rr_rel %.3e pAp %.3e alpha %.3e "
@@ -1072,7 +1220,11 @@ extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const
                         h.restarts[k], h.rr[k], h.rr_rel[k], h.pAp[k], h.alpha[k], h.beta[k], h.rr_true[k],
                         h.bb[k], h.scale[k]);
         }
-        if (h.flags) break;
+        if (h.flags) {
+            stop = true;
+            return HISQ_OK;
+        }
+        const double d2 = prm.reliable_delta * prm.reliable_delta;
         bool need = since_rel >= prm.reliable_every || iter >= prm.maxiter;
         bool restarted[kMaxRhs];
         for (int k = 0; k < n; ++k) {
@@ -1104,42 +1256,180 @@ extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const
                     bad_updates[k] = 0;
                 if (bad_updates[k] >= 3) result = HISQ_EBREAKDOWN;
             }
-            if (result == HISQ_EBREAKDOWN) break;
         }
+        update_stop();
+        return HISQ_OK;
     }
-    if (result == HISQ_ENOCONV) {
+
+    // Copy the solution out, fill stats and return the status of the solve.
+    hisq_status finish(hisq_cg_stats* stats, cudaStream_t s) {
+        if (result == HISQ_ENOCONV) {
+            for (int k = 0; k < n; ++k)
+                if (w->cg_host->active[k]) iters_k[k] = iter;
+        }
+        if (w->cg_host->flags) {
+            // fold what the low-precision solution gathered so far into x
+            HISQ_CUDA(launch_accum_solution(sv.blas(), sv.prec, w->x_hi, w->x_lo, s));
+            HISQ_CUDA(sv.poll(s));
+        }
+        const CgScalars& h = *w->cg_host;
+        hisq_status res = result;
+        if (h.flags & kFlagTimeout)
+            res = fail(HISQ_ETIMEOUT, "a bounded device-side wait gave up");
+        else if (h.flags & kFlagNaN)
+            res = fail(HISQ_ENAN, "non-finite value in the CG (source or residual)");
+        else if ((h.flags & kFlagBreakdown) || res == HISQ_EBREAKDOWN)
+            res = fail(HISQ_EBREAKDOWN, "CG breakdown: <p, A p> <= 0 repeatedly with no FP64 progress");
+        else if (res == HISQ_ENOCONV)
+            fail(HISQ_ENOCONV, "CG did not converge in %d iterations", prm.maxiter);
+        double2* xsrc = w->x_hi;
+        if (soa) {
+            HISQ_CUDA(launch_transpose_spinor(w->x_hi, w->t_hi, n, halves, g->g.vh, 0, s));
+            xsrc = w->t_hi;
+        }
         for (int k = 0; k < n; ++k)
-            if (w->cg_host->active[k]) iters_k[k] = iter;
-    }
-    if (w->cg_host->flags) {
-        // fold what the low-precision solution gathered so far into x
-        HISQ_CUDA(launch_accum_solution(sv.blas(), sv.prec, w->x_hi, w->x_lo, s));
-        HISQ_CUDA(sv.poll(s));
-    }
-    const CgScalars& h = *w->cg_host;
-    if (h.flags & kFlagNaN)
-        result = fail(HISQ_ENAN, "non-finite value in the CG (source or residual)");
-    else if ((h.flags & kFlagBreakdown) || result == HISQ_EBREAKDOWN)
-        result = fail(HISQ_EBREAKDOWN, "CG breakdown: <p, A p> <= 0 repeatedly with no FP64 progress");
-    else if (result == HISQ_ENOCONV)
-        fail(HISQ_ENOCONV, "CG did not converge in %d iterations", prm.maxiter);
-    double2* xsrc = w->x_hi;
-    if (soa) {
-        HISQ_CUDA(launch_transpose_spinor(w->x_hi, w->t_hi, n, halves, g->g.vh, 0, s));
-        xsrc = w->t_hi;
-    }
-    for (int k = 0; k < n; ++k)
-        HISQ_CUDA(cudaMemcpyAsync(x[k], sv.hi_ptr(xsrc, k), vec_bytes, cudaMemcpyDefault, s));
-    HISQ_CUDA(cudaStreamSynchronize(s));
-    if (stats) {
-        memset(stats, 0, sizeof(*stats));
-        for (int k = 0; k < n; ++k) {
-            stats->iters[k] = iters_k[k];
-            stats->true_rel_res[k] = h.bb[k] > 0 ? std::sqrt(h.rr_true[k] / h.bb[k]) : 0.0;
+            HISQ_CUDA(cudaMemcpyAsync(x[k], sv.hi_ptr(xsrc, k), vec_bytes, cudaMemcpyDefault, s));
+        HISQ_CUDA(cudaStreamSynchronize(s));
+        if (stats) {
+            memset(stats, 0, sizeof(*stats));
+            for (int k = 0; k < n; ++k) {
+                stats->iters[k] = iters_k[k];
+                stats->true_rel_res[k] = h.bb[k] > 0 ? std::sqrt(h.rr_true[k] / h.bb[k]) : 0.0;
+            }
+            stats->total_iters = iter;
+            stats->reliable_updates = reliable;
+            stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         }
-        stats->total_iters = iter;
-        stats->reliable_updates = reliable;
-        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return res;
+    }
+};
+
+}  // namespace
+
+extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const void* const b[],
+                                     void* const x[], int n, double tol, const hisq_cg_params* p,
+                                     hisq_cg_stats* stats, void* stream) {
+    hisq_cg_params prm;
+    hisq_status st = CgRun::check(g, mass, mu, b, x, n, tol, p, &prm);
+    if (st != HISQ_OK) return st;
+    std::lock_guard<std::mutex> lock(g->mtx);
+    cudaStream_t s = (cudaStream_t)stream;
+    CgRun run;
+    st = run.start(g, mass, mu, b, x, n, tol, prm, s);
+    if (st != HISQ_OK) return st;
+    while (!run.stop) {
+        const int chunk = run.next_chunk();
+        st = run.sv.run_chunk(chunk, prm.use_graphs != 0, s);
+        if (st != HISQ_OK) return st;
+        st = run.after_chunk(chunk, s);
+        if (st != HISQ_OK) return st;
+    }
+    return run.finish(stats, s);
+}
+
+// Several independent solves (distinct handles, e.g. lattices of uneven
+// volume) advanced together: every chunk of iterations of all unfinished
+// solves is one CUDA graph whose branches run the solves concurrently.
+extern "C" hisq_status hisq_cg_solve_batched(const hisq_cg_problem* probs, int nprob,
+                                             const hisq_cg_params* p, hisq_cg_stats* stats,
+                                             void* stream) {
+    if (!probs || nprob < 1 || nprob > 64) return fail(HISQ_EINVAL, "nprob must be 1..64");
+    std::vector<hisq_cg_params> prm(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        const hisq_cg_problem& q = probs[i];
+        hisq_status st = CgRun::check(q.g, q.mass, q.mu, q.b, q.x, q.n, q.tol, p, &prm[i]);
+        if (st != HISQ_OK) return st;
+        for (int j = 0; j < i; ++j)
+            if (probs[j].g == q.g) return fail(HISQ_EINVAL, "problems %d and %d share a handle", j, i);
+    }
+    // lock the handles in address order
+    std::vector<hisq_gauge> order;
+    for (int i = 0; i < nprob; ++i) order.push_back(probs[i].g);
+    std::sort(order.begin(), order.end());
+    std::vector<std::unique_lock<std::mutex>> locks;
+    for (hisq_gauge h : order) locks.emplace_back(h->mtx);
+
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<CgRun> runs(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        const hisq_cg_problem& q = probs[i];
+        hisq_status st = runs[i].start(q.g, q.mass, q.mu, q.b, q.x, q.n, q.tol, prm[i], s);
+        if (st != HISQ_OK) return st;
+    }
+    const bool graphs = (p ? p->use_graphs : 1) != 0;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join(nprob, nullptr);
+    std::map<std::pair<unsigned long long, int>, cudaGraphExec_t> cache;
+    auto cleanup = [&]() {
+        for (auto& kv : cache) cudaGraphExecDestroy(kv.second);
+        for (cudaEvent_t e : join)
+            if (e) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (cap) cudaStreamDestroy(cap);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < nprob && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(HISQ_ECUDA, "batched solve set-up failed: %s", cudaGetErrorString(e));
+    }
+    hisq_status st = HISQ_OK;
+    while (st == HISQ_OK) {
+        unsigned long long mask = 0;
+        int chunk = 1 << 30;
+        for (int i = 0; i < nprob; ++i)
+            if (!runs[i].stop) {
+                mask |= 1ull << i;
+                chunk = std::min(chunk, runs[i].next_chunk());
+            }
+        if (mask == 0) break;
+        if (graphs) {
+            auto key = std::make_pair(mask, chunk);
+            auto it = cache.find(key);
+            if (it == cache.end()) {
+                cudaGraph_t graph = nullptr;
+                e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) e = cudaEventRecord(fork, cap);
+                for (int i = 0; i < nprob && e == cudaSuccess; ++i) {
+                    if (!(mask >> i & 1)) continue;
+                    cudaStream_t si = runs[i].w->cap_stream;
+                    e = cudaStreamWaitEvent(si, fork, 0);
+                    for (int c = 0; c < chunk && e == cudaSuccess; ++c) e = runs[i].sv.iterate(si);
+                    if (e == cudaSuccess) e = cudaEventRecord(join[i], si);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join[i], 0);
+                }
+                cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+                if (e == cudaSuccess) e = e2;
+                cudaGraphExec_t exec = nullptr;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e != cudaSuccess) {
+                    st = fail(HISQ_ECUDA, "batched graph capture failed: %s", cudaGetErrorString(e));
+                    break;
+                }
+                it = cache.emplace(key, exec).first;
+            }
+            e = cudaGraphLaunch(it->second, s);
+        } else {
+            for (int i = 0; i < nprob && e == cudaSuccess; ++i)
+                if (mask >> i & 1)
+                    for (int c = 0; c < chunk && e == cudaSuccess; ++c) e = runs[i].sv.iterate(s);
+        }
+        if (e != cudaSuccess) {
+            st = fail(HISQ_ECUDA, "batched iteration launch failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        for (int i = 0; i < nprob && st == HISQ_OK; ++i)
+            if (mask >> i & 1) st = runs[i].after_chunk(chunk, s);
+    }
+    cleanup();
+    if (st != HISQ_OK) return st;
+    hisq_status result = HISQ_OK;
+    for (int i = 0; i < nprob; ++i) {
+        hisq_status r = runs[i].finish(stats ? &stats[i] : nullptr, s);
+        if (result == HISQ_OK && r != HISQ_OK) result = r;
     }
     return result;
 }

@@ -164,7 +164,7 @@ enum Epi : int { EPI_NONE = 0, EPI_X = 1, EPI_XY = 2 };
 // the register kernel, 1 the register kernel with packed f32x2 complex
 // arithmetic (FP32 arithmetic only), 2 the kernel with links staged in shared
 // memory by bulk copies (FP32 arithmetic only).
-enum DslashKind : int { KIND_REG = 0, KIND_PACKED = 1, KIND_STAGED = 2 };
+enum DslashKind : int { KIND_REG = 0, KIND_PACKED = 1, KIND_STAGED = 2, KIND_PIPE1 = 3, KIND_PIPE2 = 4 };
 struct DslashTune {
     int rpt;
     int minb;

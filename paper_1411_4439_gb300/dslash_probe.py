@@ -35,6 +35,7 @@ def main(argv=None):
     ap.add_argument("--pack", type=int, default=0)
     ap.add_argument("--prefetch", type=int, default=0)
     ap.add_argument("--staged", type=int, default=0, help="4 = links staged in shared memory")
+    ap.add_argument("--pipe", type=int, default=0, help="1 or 2: loads of the next 1 or 2 hops in flight")
     ap.add_argument("--layout", choices=["aos", "soa"], default="soa")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
@@ -54,10 +55,11 @@ def main(argv=None):
     g = H.hisq_gauge_load(L, torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev), prec=prec,
                           recon_U=a.recon[0] if prec else 18, recon_N=a.recon[1] if prec else 18)
     del U, N
-    if a.rpt or a.pack or a.prefetch or a.staged:
+    if a.rpt or a.pack or a.prefetch or a.staged or a.pipe:
+        pipe = {0: 0, 1: H.hisq.HISQ_MAP_PIPELINED, 2: H.hisq.HISQ_MAP_PIPELINED2}[a.pipe]
         H.hisq_set_dslash_mapping(g, a.rpt, a.minb, a.pack * H.hisq.HISQ_MAP_PACKED
                                   + a.prefetch * H.hisq.HISQ_MAP_L2_PREFETCH
-                                  + (H.hisq.HISQ_MAP_STAGED if a.staged else 0))
+                                  + (H.hisq.HISQ_MAP_STAGED if a.staged else 0) + pipe)
     mapping = H.hisq_get_dslash_mapping(g, a.n, prec)
     vh = int(np.prod(L)) // 2
     if a.prec == "f64":
@@ -93,7 +95,7 @@ def main(argv=None):
     print(json.dumps({"lattice": L, "n": a.n, "prec": a.prec, "recon": [fu, fn], "op": a.op,
                       "rpt": mapping[0], "minb": mapping[1], "flags": mapping[2],
                       "staged": bool(mapping[2] & H.hisq.HISQ_MAP_STAGED),
-                      "pack": a.pack, "prefetch": a.prefetch,
+                      "pack": a.pack, "prefetch": a.prefetch, "pipe": a.pipe,
                       "layout": a.layout,
                       "us_per_launch": t * 1e6 / ops, "alg_bytes_per_dslash": nb,
                       "alg_gbs": nb * ops / t / 1e9, "gflops": 1146 * a.n * vh * ops / t / 1e9}))

@@ -37,13 +37,15 @@ MAX_RHS = 16
 HISQ_OP_M, HISQ_OP_MDAG, HISQ_OP_DM_DMU = 0, 1, 2
 HISQ_OP_D2M_DMU2, HISQ_OP_D3M_DMU3, HISQ_OP_D4M_DMU4 = 3, 4, 5
 HISQ_MAP_PACKED, HISQ_MAP_L2_PREFETCH, HISQ_MAP_STAGED = 1, 2, 4
+HISQ_MAP_PIPELINED, HISQ_MAP_PIPELINED2 = 8, 16
 
 EXPORTED = ["hisq_version", "hisq_last_error", "hisq_gauge_load", "hisq_gauge_free",
             "hisq_gauge_info", "hisq_set_dslash_mapping", "hisq_get_dslash_mapping",
+            "hisq_autotune_dslash",
             "hisq_link_compress",
             "hisq_link_reconstruct", "hisq_dslash", "hisq_dslash_ex", "hisq_mdagm",
             "hisq_apply_m", "hisq_link_force", "hisq_cdot", "hisq_cdot_noalloc",
-            "hisq_cg_default_params", "hisq_cg_solve"]
+            "hisq_cg_default_params", "hisq_cg_solve", "hisq_cg_solve_batched"]
 
 
 class HisqError(RuntimeError):
@@ -65,6 +67,12 @@ class hisq_cg_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * MAX_RHS), ("total_iters", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int),
                 ("true_rel_res", ctypes.c_double * MAX_RHS), ("seconds", ctypes.c_double)]
+
+
+class hisq_cg_problem(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_void_p), ("mass", ctypes.c_double), ("mu", ctypes.c_double),
+                ("b", ctypes.POINTER(ctypes.c_void_p)), ("x", ctypes.POINTER(ctypes.c_void_p)),
+                ("n", ctypes.c_int), ("tol", ctypes.c_double)]
 
 
 _lib = None
@@ -89,6 +97,8 @@ def library() -> ctypes.CDLL:
         "hisq_gauge_info": (c_int, [vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_size_t)]),
         "hisq_set_dslash_mapping": (c_int, [vp, c_int, c_int, c_int]),
         "hisq_get_dslash_mapping": (c_int, [vp, c_int, c_int, ip, ip, ip]),
+        "hisq_autotune_dslash": (c_int, [vp, c_int, c_int, c_int, c_int, ip, ip, ip,
+                                         ctypes.POINTER(c_double)]),
         "hisq_link_compress": (c_int, [ip, vp, c_int, vp, ctypes.POINTER(c_double), vp]),
         "hisq_link_reconstruct": (c_int, [ip, vp, c_int, vp, vp]),
         "hisq_dslash": (c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int, c_int, vp]),
@@ -104,6 +114,9 @@ def library() -> ctypes.CDLL:
         "hisq_cdot_noalloc": (c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, ctypes.c_longlong,
                                       ctypes.POINTER(c_double), vp]),
         "hisq_cg_default_params": (None, [ctypes.POINTER(hisq_cg_params)]),
+        "hisq_cg_solve_batched": (c_int, [ctypes.POINTER(hisq_cg_problem), c_int,
+                                          ctypes.POINTER(hisq_cg_params), ctypes.POINTER(hisq_cg_stats),
+                                          vp]),
         "hisq_cg_solve": (c_int, [vp, c_double, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
                                   c_double, ctypes.POINTER(hisq_cg_params),
                                   ctypes.POINTER(hisq_cg_stats), vp]),
@@ -258,6 +271,16 @@ def hisq_get_dslash_mapping(g: Gauge, n: int, prec: int) -> tuple:
     return r.value, b.value, f.value
 
 
+def hisq_autotune_dslash(g: Gauge, n: int, prec: int, layout: int = HISQ_SOA, reps: int = 5) -> dict:
+    """Time every built Dslash mapping for (n, prec, layout), keep the fastest on g."""
+    r, b, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    sec = ctypes.c_double()
+    _check(library().hisq_autotune_dslash(g.handle, int(n), int(prec), int(layout), int(reps),
+                                          ctypes.byref(r), ctypes.byref(b), ctypes.byref(f),
+                                          ctypes.byref(sec)))
+    return dict(rhs_per_thread=r.value, min_blocks=b.value, flags=f.value, seconds=sec.value)
+
+
 def hisq_link_compress(L, links, recon, packed, stream=None) -> float:
     """Device complex128 [4][V][3][3] -> device float64 [4][V][recon]; returns max error."""
     err = ctypes.c_double()
@@ -372,3 +395,32 @@ def hisq_cg_solve(g: Gauge, mass: float, mu: float, b, x, tol: float, params=Non
                                  _stream_handle(stream, *b, *x))
     _check(st, stats)
     return stats
+
+
+def hisq_cg_solve_batched(problems, params=None, stream=None):
+    """Independent solves advanced together through one CUDA graph per chunk.
+
+    problems: list of dicts with keys g (Gauge), mass, mu, b, x (lists of
+    complex128 buffers), tol. Returns one hisq_cg_stats per problem; raises
+    HisqError (with the stats list) on any status but HISQ_OK.
+    """
+    arr = (hisq_cg_problem * len(problems))()
+    keep = []
+    bufs = []
+    for i, pr in enumerate(problems):
+        if len(pr["b"]) != len(pr["x"]):
+            raise ValueError("b and x need the same number of rhs")
+        pb, px = _ptr_array(pr["b"]), _ptr_array(pr["x"])
+        keep += [pb, px]
+        bufs += list(pr["b"]) + list(pr["x"])
+        arr[i] = hisq_cg_problem(pr["g"].handle, float(pr["mass"]), float(pr.get("mu", 0.0)),
+                                 ctypes.cast(pb, ctypes.POINTER(ctypes.c_void_p)),
+                                 ctypes.cast(px, ctypes.POINTER(ctypes.c_void_p)), len(pr["b"]),
+                                 float(pr["tol"]))
+    stats = (hisq_cg_stats * len(problems))()
+    p = params if params is not None else hisq_cg_default_params()
+    st = library().hisq_cg_solve_batched(arr, len(problems), ctypes.byref(p), stats,
+                                         _stream_handle(stream, *bufs))
+    out = [stats[i] for i in range(len(problems))]
+    _check(st, out)
+    return out

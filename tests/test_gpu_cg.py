@@ -234,3 +234,58 @@ def test_aos_and_soa_solves_agree(gpu_lib):
     for x in (xa, xs):
         assert np.all(O.true_relative_residual(A, x, b) <= 1e-10)
         assert rel_l2(x, xo) <= 1e-8
+
+
+@pytest.mark.parametrize("prec,graphs", [(1, 1), (1, 0), (2, 1)])
+def test_batched_uneven_lattices(gpu_lib, prec, graphs):
+    """Three bundles on lattices of uneven volume advanced in one batched call:
+    each meets the oracle's true residual and matches its single solve."""
+    import torch
+    H = gpu_lib
+    cases = [((4, 4, 4, 4), 3, 0.05, 11), ((4, 6, 8, 10), 4, 0.02, 12), ((6, 6, 6, 8), 2, 0.1, 13)]
+    handles, probs, data = [], [], []
+    try:
+        for L, n, m, seed in cases:
+            U, N = gen.hisq_links(L, seed=seed)
+            b = gen.z2_source(L, n, seed=seed + 100)
+            g = H.hisq_gauge_load(L, dev(U), dev(N), prec=prec, recon_U=18, recon_N=14)
+            handles.append(g)
+            bt = [dev(b[k]) for k in range(n)]
+            xt = [torch.zeros_like(t) for t in bt]
+            probs.append(dict(g=g, mass=m, mu=0.0, b=bt, x=xt, tol=1e-10))
+            data.append((L, U, N, b, m))
+        p = H.cg_params(inner_prec=prec, even_odd=1, use_graphs=graphs)
+        stats = H.hisq_cg_solve_batched(probs, p)
+        for (L, U, N, b, m), pr, st in zip(data, probs, stats):
+            x = np.stack([t.cpu().numpy() for t in pr["x"]])
+            xo, A = oracle_solution(U, N, L, b, m)
+            res = O.true_relative_residual(A, x, b)
+            assert np.all(res <= 1e-10), (L, res)
+            for k in range(len(x)):
+                assert rel_l2(x[k], xo[k]) <= 1e-8
+                assert abs(st.true_rel_res[k] - res[k]) <= 1e-11
+            xs, ss = solve(H, L, U, N, b, m, prec=prec, use_graphs=graphs)
+            assert rel_l2(x, xs) <= 1e-8
+            # host decisions fall on the shortest chunk of the batch, so the
+            # iteration counts may differ from the single solve by a few
+            for k in range(len(x)):
+                assert abs(st.iters[k] - ss.iters[k]) <= max(5, ss.iters[k] // 10)
+    finally:
+        for g in handles:
+            H.hisq_gauge_free(g)
+
+
+def test_batched_rejects_shared_handle(gpu_lib):
+    import torch
+    H = gpu_lib
+    L = (4, 4, 4, 4)
+    U, N = gen.hisq_links(L, seed=3)
+    g = H.hisq_gauge_load(L, dev(U), dev(N), prec=1)
+    try:
+        b = [dev(gen.z2_source(L, 1, seed=4)[0])]
+        pr = dict(g=g, mass=0.1, mu=0.0, b=b, x=[torch.zeros_like(b[0])], tol=1e-10)
+        with pytest.raises(H.HisqError) as ei:
+            H.hisq_cg_solve_batched([pr, dict(pr)], H.cg_params(inner_prec=1))
+        assert ei.value.status == H.hisq.HISQ_EINVAL
+    finally:
+        H.hisq_gauge_free(g)

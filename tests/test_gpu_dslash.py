@@ -340,3 +340,96 @@ def test_staged_cg_solve_matches_oracle(gpu_lib):
         H.hisq_gauge_free(g)
     res = O.true_relative_residual(lambda q: O.apply_Ae(U, N, q, L, m), x, b)
     assert np.all(res <= 1e-10)
+
+
+def test_autotuner_keeps_a_correct_mapping(gpu_lib):
+    import torch
+    H = gpu_lib
+    L = (16, 16, 4, 6)
+    U, N = links(L)
+    g = load(H, L, 1, 18, 14)
+    try:
+        for n in (8, 4, 3):
+            best = H.hisq.hisq_autotune_dslash(g, n, 1, H.HISQ_AOS, reps=3)
+            assert best["seconds"] > 0
+            got = H.hisq_get_dslash_mapping(g, n, 1)
+            assert got == (best["rhs_per_thread"], best["min_blocks"], best["flags"])
+            v = gen.gaussian_source(L, n, seed=90 + n)
+            vd = [to_dev(v[k], 1) for k in range(n)]
+            wd = [torch.full_like(t, float("nan")) for t in vd]
+            H.hisq_dslash(g, vd, wd, 1, 1)
+            torch.cuda.synchronize()
+            ref = O.dslash_parity(U, N, v, L, 1)
+            for k in range(n):
+                assert rel_l2(from_dev(wd[k]), ref[k]) < 1e-6
+    finally:
+        H.hisq_gauge_free(g)
+
+
+PIPE_MAPPINGS = [(8, 1, 1), (4, 2, 1), (4, 1, 2), (4, 2, 2)]   # (rpt, minb, depth)
+
+
+@pytest.mark.parametrize("prec,ru,rn", [(1, 18, 14), (1, 12, 14), (1, 18, 18), (1, 14, 14),
+                                        (2, 18, 14), (2, 12, 14)])
+def test_pipelined_kernel_matches_oracle(gpu_lib, prec, ru, rn):
+    """Loads of the next hops in flight: every built mapping, both layouts, mu, parities,
+    bundles that use one and two rhs groups, on a lattice with a ragged last block."""
+    import torch
+    H = gpu_lib
+    L = (6, 10, 4, 6)                       # V_h = 720: not a multiple of the block
+    U, N = links(L)
+    g = load(H, L, prec, ru, rn)
+    try:
+        for rpt, minb, depth in PIPE_MAPPINGS:
+            flag = H.HISQ_MAP_PIPELINED if depth == 1 else H.HISQ_MAP_PIPELINED2
+            H.hisq_set_dslash_mapping(g, rpt, minb, flag)
+            for n in sorted({rpt, 2 * rpt}):
+                assert H.hisq_get_dslash_mapping(g, n, prec) == (rpt, minb, flag)
+                v = gen.gaussian_source(L, n, seed=90 + n)
+                for layout in (H.HISQ_AOS, H.HISQ_SOA):
+                    for parity, mu in ((0, 0.0), (1, 0.0), (1, -0.25)):
+                        src = v if layout == H.HISQ_AOS else np.ascontiguousarray(np.swapaxes(v, 1, 2))
+                        vd = [to_dev(src[k], prec) for k in range(n)]
+                        wd = [torch.full_like(t, float("nan")) for t in vd]
+                        H.hisq_dslash_ex(g, mu, vd, wd, parity, prec, layout)
+                        torch.cuda.synchronize()
+                        ref = O.dslash_parity(U, N, v, L, parity, mu)
+                        for k in range(n):
+                            got = from_dev(wd[k])
+                            got = got if layout == H.HISQ_AOS else np.swapaxes(got, 0, 1)
+                            assert rel_l2(got, ref[k]) < TOL[prec], (rpt, minb, depth, n, layout, parity, mu, k)
+    finally:
+        H.hisq_gauge_free(g)
+
+
+def test_pipelined_mapping_in_solve_and_mu_derivative(gpu_lib):
+    """The CG runs the pipelined kernel; the temporal-only operator d M / d mu,
+    which the pipelined kernel does not serve, falls back to the register kernel."""
+    import torch
+    H = gpu_lib
+    L, m, mu = (8, 8, 8, 8), 0.05, 0.2
+    U, N = links(L)
+    b = gen.z2_source(L, 8, seed=91)
+    g = load(H, L, 1, 18, 14)
+    try:
+        H.hisq_set_dslash_mapping(g, 8, 1, H.HISQ_MAP_PIPELINED)
+        bt = [torch.from_numpy(b[k]).cuda() for k in range(8)]
+        xt = [torch.zeros_like(t) for t in bt]
+        H.hisq_cg_solve(g, m, 0.0, bt, xt, 1e-10, H.cg_params(inner_prec=1))
+        x = np.stack([t.cpu().numpy() for t in xt])
+        v = O.to_full(gen.gaussian_source(L, 8, seed=92), L, 0) + \
+            O.to_full(gen.gaussian_source(L, 8, seed=93), L, 1)
+        vb = np.concatenate([O.to_half(v, L, 0), O.to_half(v, L, 1)], axis=1)
+        src = [torch.from_numpy(vb[k]).cuda().to(torch.complex64) for k in range(8)]
+        for op, order in ((H.HISQ_OP_M, 0), (H.HISQ_OP_DM_DMU, 1)):
+            w = [torch.empty_like(t) for t in src]
+            H.hisq_apply_m(g, m, mu, op, src, w, 1)
+            torch.cuda.synchronize()
+            ref = O.apply_M(U, N, v, m, mu) if order == 0 else O.apply_dnM_dmun(U, N, v, mu, 1)
+            exp = np.concatenate([O.to_half(ref, L, 0), O.to_half(ref, L, 1)], axis=1)
+            for k in range(8):
+                assert rel_l2(w[k].cpu().numpy(), exp[k]) < 1e-6, (op, k)
+    finally:
+        H.hisq_gauge_free(g)
+    res = O.true_relative_residual(lambda q: O.apply_Ae(U, N, q, L, m), x, b)
+    assert np.all(res <= 1e-10)
