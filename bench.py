@@ -161,6 +161,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of one launch of the bench's roofline Dslash, from
+# one ncu capture of that kernel (profiles/dslash_f32_r18_r14_n8_32x32x32x8_pipelined.md),
+# keyed by (lattice, rhs per thread, min blocks, mapping flags). A mapping
+# without a capture reports null.
+DSLASH_TRAFFIC = {((32, 32, 32, 8), 4, 2, 16): 159_459_072 + 5_535_744}
+
+
+def dslash_kernel_name(rpt, minb, flags, L):
+    if flags & 16:
+        name = f"dslash_pipe_kernel<float,float,18,14,rpt={rpt},minb={minb},depth=2,EPI_NONE,AoS>"
+    elif flags & 8:
+        name = f"dslash_pipe_kernel<float,float,18,14,rpt={rpt},minb={minb},depth=1,EPI_NONE,AoS>"
+    elif flags & 4:
+        name = f"dslash_staged_kernel<float,float,18,14,rpt={rpt},minb={minb},EPI_NONE,AoS>"
+    else:
+        name = f"dslash_kernel<float,float,18,14,rpt={rpt},minb={minb},EPI_NONE,AoS>"
+    lat = "x".join(str(v) for v in L)
+    return f"{name} n={NRHS} on {lat}", DSLASH_TRAFFIC.get((tuple(L), rpt, minb, flags))
+
+
 def measured_peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -288,6 +308,8 @@ def run_gpu(args):
         return t, nbytes, flops
 
     t_d, bytes_d, flops_d = time_dslash(NRHS)
+    rpt_d, minb_d, flags_d = H.hisq_get_dslash_mapping(g, NRHS, H.HISQ_F32)
+    kernel_d, traffic_d = dslash_kernel_name(rpt_d, minb_d, flags_d, L)
     gbs = bytes_d / t_d / 1e9
     sweep = {}
     for n in (1, 2, 4, 16):
@@ -343,8 +365,8 @@ def run_gpu(args):
                "max_true_rel_res": max(res), "wall_s_per_step": wall / args.steps},
         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
-                     "traffic": None,
-                     "kernel": "dslash_kernel<float,float,18,14,rpt,EPI_NONE> n=8 on 32^3x8",
+                     "traffic": traffic_d,
+                     "kernel": kernel_d,
                      "peak_source": peaks["source"],
                      "bytes_per_launch": bytes_d},
         "dslash": {"gbs": round(gbs, 1), "frac_of_8tbs": round(gbs / NOMINAL_HBM_GBS, 4),
@@ -402,16 +424,253 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# further workloads (not the default headline line): --workload <name>
+# ---------------------------------------------------------------------------
+
+def _time_solve(H, torch, g, mass, mu, bt, xt, tol, params, stream, reps=1):
+    """CUDA-event seconds of one hisq_cg_solve (after one warm-up) and its stats."""
+    st = H.hisq_cg_solve(g, mass, mu, bt, xt, tol, params, stream=stream)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = H.hisq_cg_solve(g, mass, mu, bt, xt, tol, params, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(ts), st
+
+
+def _cg_line(name, lattice, n, inner, t, st, extra=None):
+    d = {"workload": name, "lattice": list(lattice), "nrhs": n, "inner_prec": inner,
+         "s_per_solve": t, "s_per_rhs": t / n, "iterations": st.total_iters,
+         "reliable_updates": st.reliable_updates,
+         "max_true_rel_res": max(st.true_rel_res[k] for k in range(n))}
+    if extra:
+        d.update(extra)
+    print(json.dumps(d), flush=True)
+
+
+def run_cg_configs(args):
+    """CG seconds per rhs on the listed configurations: FP64 8^4 single rhs;
+    FP32 32^3x8 with n = 1, 2, 4, 8 (and the FP64 single-rhs solve); FP16
+    48^3x12 with n = 8 Gaussian sources at m = 0.0025 against the FP64
+    single-rhs solve of source 0; FP64 16^4 full-lattice solve at mu = 0.1."""
+    import torch
+
+    import hisq_inputs as gen
+    import paper_1411_4439_gb300 as H
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    H.hisq.library()
+
+    def dev_list(a):
+        return [torch.from_numpy(np.ascontiguousarray(a[k])).to(dev) for k in range(a.shape[0])]
+
+    # 8^4, FP64, one rhs, seed 0, m = 0.05
+    L0 = (8, 8, 8, 8)
+    U, N = gen.hisq_links(L0, seed=0)
+    g = H.hisq_gauge_load(L0, torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev), prec=H.HISQ_F64)
+    bt = dev_list(gen.z2_source(L0, 1, seed=0))
+    xt = [torch.zeros_like(bt[0])]
+    t, st = _time_solve(H, torch, g, 0.05, 0.0, bt, xt, TOL, H.cg_params(inner_prec=H.HISQ_F64), stream, 3)
+    _cg_line("fp64 8^4 m=0.05", L0, 1, "f64", t, st)
+    H.hisq_gauge_free(g)
+
+    # 32^3x8, FP32 inner, n = 1, 2, 4, 8, and FP64 single rhs
+    U, N = gen.hisq_links(L, seed=LINK_SEED)
+    dU, dN = torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev)
+    b = gen.z2_source(L, NRHS, seed=SOURCE_SEED)
+    g = H.hisq_gauge_load(L, dU, dN, prec=H.HISQ_F32, recon_U=18, recon_N=14)
+    for n in (1, 2, 4, 8):
+        bt = dev_list(b[:n])
+        xt = [torch.zeros_like(x) for x in bt]
+        t, st = _time_solve(H, torch, g, MASS, 0.0, bt, xt, TOL,
+                            H.cg_params(inner_prec=H.HISQ_F32, reliable_every=RELIABLE_EVERY), stream)
+        _cg_line("fp32 32^3x8 m=0.01", L, n, "f32", t, st)
+    H.hisq_gauge_free(g)
+    g = H.hisq_gauge_load(L, dU, dN, prec=H.HISQ_F64)
+    bt = dev_list(b[:1])
+    xt = [torch.zeros_like(bt[0])]
+    t, st = _time_solve(H, torch, g, MASS, 0.0, bt, xt, TOL, H.cg_params(inner_prec=H.HISQ_F64), stream)
+    _cg_line("fp64 32^3x8 m=0.01", L, 1, "f64", t, st)
+    H.hisq_gauge_free(g)
+    del dU, dN
+
+    # 48^3x12, FP16 storage / FP32 arithmetic, n = 8 Gaussian, m = 0.0025; FP64 single rhs
+    L2 = (48, 48, 48, 12)
+    U, N = gen.hisq_links(L2, seed=LINK_SEED)
+    dU, dN = torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev)
+    del U, N
+    b = gen.gaussian_source(L2, 8, seed=SOURCE_SEED)
+    g = H.hisq_gauge_load(L2, dU, dN, prec=H.HISQ_F16, recon_U=18, recon_N=14)
+    bt = dev_list(b)
+    xt = [torch.zeros_like(x) for x in bt]
+    t16, st16 = _time_solve(H, torch, g, 0.0025, 0.0, bt, xt, TOL, H.cg_params(inner_prec=H.HISQ_F16), stream)
+    H.hisq_gauge_free(g)
+    g = H.hisq_gauge_load(L2, dU, dN, prec=H.HISQ_F64)
+    x64 = [torch.zeros_like(bt[0])]
+    t64, st64 = _time_solve(H, torch, g, 0.0025, 0.0, bt[:1], x64, TOL, H.cg_params(inner_prec=H.HISQ_F64), stream)
+    diff = float(torch.linalg.vector_norm(xt[0] - x64[0]) / torch.linalg.vector_norm(x64[0]))
+    _cg_line("fp16 48^3x12 m=0.0025 gaussian", L2, 8, "f16", t16, st16,
+             {"fp64_single_rhs_s": t64, "fp64_iterations": st64.total_iters,
+              "mixed_over_fp64_s_per_rhs": (t16 / 8) / t64, "rhs0_rel_diff_vs_fp64": diff})
+    H.hisq_gauge_free(g)
+    del dU, dN
+
+    # 16^4, FP64, n = 4 Z2, mu = 0.1, full-lattice M^dag M, m = 0.05
+    L3 = (16, 16, 16, 16)
+    U, N = gen.hisq_links(L3, seed=LINK_SEED)
+    g = H.hisq_gauge_load(L3, torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev), prec=H.HISQ_F64)
+    vh = int(np.prod(L3)) // 2
+    bz = gen.z2_source(L3, 4, seed=SOURCE_SEED)
+    bfull = np.concatenate([bz, gen.z2_source(L3, 4, seed=SOURCE_SEED + 7)], axis=1)
+    assert bfull.shape[1] == 2 * vh
+    bt = dev_list(bfull)
+    xt = [torch.zeros_like(x) for x in bt]
+    t, st = _time_solve(H, torch, g, 0.05, 0.1, bt, xt, TOL,
+                        H.cg_params(inner_prec=H.HISQ_F64, even_odd=0), stream)
+    _cg_line("fp64 16^4 mu=0.1 full lattice", L3, 4, "f64", t, st)
+    H.hisq_gauge_free(g)
+
+
+def run_dslash_sweep(args):
+    """Autotuned Dslash (AoS spinors) for n = 1..16 on 48^3x12 and 64^3x16 in
+    FP64 18/18, FP32 18/14, FP16 18/14 and FP16 12/14: time per launch,
+    algorithmic GB/s and its fraction of the measured HBM peak, GFlop/s."""
+    import torch
+
+    import hisq_inputs as gen
+    import paper_1411_4439_gb300 as H
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    H.hisq.library()
+    peak = measured_peaks()
+    sizes = {H.HISQ_F64: 8, H.HISQ_F32: 4, H.HISQ_F16: 2}
+    names = {H.HISQ_F64: "f64", H.HISQ_F32: "f32", H.HISQ_F16: "f16"}
+    dtypes = {H.HISQ_F64: torch.complex128, H.HISQ_F32: torch.complex64, H.HISQ_F16: torch.float16}
+    lattices = [tuple(int(x) for x in s.split("x")) for s in args.lattices.split(",")]
+    for Ls in lattices:
+        U, N = gen.hisq_links(Ls, seed=LINK_SEED)
+        dU, dN = torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev)
+        del U, N
+        vh = int(np.prod(Ls)) // 2
+        for prec, ru, rn in ((H.HISQ_F64, 18, 18), (H.HISQ_F32, 18, 14), (H.HISQ_F16, 18, 14),
+                             (H.HISQ_F16, 12, 14)):
+            g = H.hisq_gauge_load(Ls, dU, dN, prec=prec, recon_U=ru, recon_N=rn)
+            for n in (1, 2, 4, 8, 16):
+                shape = (vh, 3, 2) if prec == H.HISQ_F16 else (vh, 3)
+                vs = [torch.randn(shape, dtype=torch.float32, device=dev).to(dtypes[prec]) if prec == H.HISQ_F16
+                      else torch.randn(shape, dtype=dtypes[prec], device=dev) for _ in range(n)]
+                ws = [torch.empty_like(v) for v in vs]
+                tune = H.hisq_autotune_dslash(g, n, prec, H.HISQ_AOS, 5)
+                for _ in range(3):
+                    H.hisq_dslash(g, vs, ws, 0, prec, stream=stream)
+                reps = 20
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    H.hisq_dslash(g, vs, ws, 0, prec, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                t = e0.elapsed_time(e1) / 1e3 / reps
+                nb = dslash_bytes_per_site(n, ru, rn, sizes[prec], sizes[prec]) * vh
+                print(json.dumps({"workload": "dslash sweep", "lattice": list(Ls), "prec": names[prec],
+                                  "recon": [ru, rn], "n": n, "us": round(t * 1e6, 2),
+                                  "alg_gbs": round(nb / t / 1e9, 1),
+                                  "frac_of_measured_hbm": round(nb / t / 1e9 / peak["hbm_gbs"], 4),
+                                  "gflops": round(DSLASH_FLOPS_PER_SITE_RHS * n * vh / t / 1e9, 1),
+                                  "mapping": [tune["rhs_per_thread"], tune["min_blocks"], tune["flags"]]}),
+                      flush=True)
+                del vs, ws
+            H.hisq_gauge_free(g)
+        del dU, dN
+        torch.cuda.empty_cache()
+
+
+def run_batched(args):
+    """Three gauge fields of uneven volume solved by one hisq_cg_solve_batched
+    call (one CUDA graph per chunk of iterations): 24^3x6 with n = 16
+    (m = 0.002), 32^3x8 with n = 8 (m = 0.01), 64^3x16 with n = 4 (m = 0.01);
+    FP16 storage with FP32 arithmetic and FP64 reliable updates, Z2 sources,
+    link compression and thread mapping chosen by the autotuner. Also times
+    the same three solves one after another."""
+    import torch
+
+    import hisq_inputs as gen
+    import paper_1411_4439_gb300 as H
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    H.hisq.library()
+    cases = [((24, 24, 24, 6), 16, 0.002), ((32, 32, 32, 8), 8, 0.01), ((64, 64, 64, 16), 4, 0.01)]
+    handles, probs, tuned = [], [], []
+    for i, (Ls, n, m) in enumerate(cases):
+        U, N = gen.hisq_links(Ls, seed=LINK_SEED)
+        dU, dN = torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev)
+        del U, N
+        g = H.hisq_gauge_load_tuned(Ls, dU, dN, prec=H.HISQ_F16, n=n)
+        del dU, dN
+        handles.append(g)
+        bundle = H.hisq_autotune_bundle(g, n, H.HISQ_F16)
+        tuned.append({"lattice": list(Ls), "n": n, "mass": m, "recon": [g.recon_U, g.recon_N],
+                      "mapping": list(H.hisq_get_dslash_mapping(g, n, H.HISQ_F16)),
+                      "bundle_tuner_best_n": bundle["n"]})
+        b = gen.z2_source(Ls, n, seed=SOURCE_SEED + i)
+        bt = [torch.from_numpy(b[k]).to(dev) for k in range(n)]
+        probs.append(dict(g=g, mass=m, mu=0.0, b=bt, x=[torch.zeros_like(t) for t in bt], tol=TOL))
+        torch.cuda.empty_cache()
+    params = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=RELIABLE_EVERY)
+    H.hisq_cg_solve_batched(probs, params, stream=stream)        # warm-up (graphs, workspaces)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = H.hisq_cg_solve_batched(probs, params, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    t_batched = e0.elapsed_time(e1) / 1e3
+    e0.record(stream)
+    for pr in probs:
+        H.hisq_cg_solve(pr["g"], pr["mass"], 0.0, pr["b"], pr["x"], TOL, params, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    nrhs = sum(n for _, n, _ in cases)
+    for tinfo, st, (Ls, n, m) in zip(tuned, stats, cases):
+        tinfo.update({"iterations": st.total_iters, "reliable_updates": st.reliable_updates,
+                      "max_true_rel_res": max(st.true_rel_res[k] for k in range(n))})
+    print(json.dumps({"workload": "batched uneven lattices, FP16 inner", "s_batched": t_batched,
+                      "s_sequential": t_seq, "s_per_rhs_batched": t_batched / nrhs, "nrhs": nrhs,
+                      "problems": tuned}), flush=True)
+    for g in handles:
+        H.hisq_gauge_free(g)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=["headline", "cg-configs", "dslash-sweep", "batched"],
+                    default="headline", help="headline = the one JSON line of the contract")
+    ap.add_argument("--lattices", default="48x48x48x12,64x64x64x16",
+                    help="lattices of the Dslash sweep (Lx x Ly x Lz x Lt, comma separated)")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "cg-configs":
+        run_cg_configs(args)
+    elif args.workload == "dslash-sweep":
+        run_dslash_sweep(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_gpu(args)
 

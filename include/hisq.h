@@ -102,6 +102,12 @@ const char* hisq_last_error(void);
  * [parity][mu][complex component][V_h] in precision `prec`, and always also
  * keeps an FP64 R18 copy used by FP64 Dslash calls and by the CG's FP64
  * reliable updates. prec == HISQ_F64 requires R18 for both fields.
+ * prec == HISQ_F16 stores every link real as a 16-bit integer q with value
+ * q * s_c, one scale s_c = max |Re|,|Im| / 32767 per stored complex
+ * component c of each field (2^-15 of the range, where IEEE half keeps only
+ * 2^-11 of each value: with IEEE half links the sloppy operator differs from
+ * the FP64 one by more than its smallest eigenvalue at light masses and the
+ * reliable-update CG diverges); FP16 spinors stay IEEE half.
  *   L          lattice extents (host array of 4 ints).
  *   U, N       canonical complex128 links, device pointers if on_device != 0,
  *              else host pointers. Read only; not retained.
@@ -155,8 +161,8 @@ hisq_status hisq_get_dslash_mapping(hisq_gauge g, int n, hisq_prec spinor_prec,
 
 /*
  * Autotuner: times `reps` Dslash launches of every built mapping that fits
- * n rhs, `spinor_prec` and `layout` on this handle (register and shared-
- * memory-staged kernels, every register budget) and keeps the fastest for
+ * n rhs, `spinor_prec` and `layout` on this handle (register, pipelined and
+ * shared-memory-staged kernels, every register budget) and keeps the fastest for
  * later calls of that shape (hisq_set_dslash_mapping still takes priority).
  * Returns the choice and its time per launch (any output may be NULL).
  * Allocates and frees scratch spinors; synchronises the device.
@@ -164,6 +170,34 @@ hisq_status hisq_get_dslash_mapping(hisq_gauge g, int n, hisq_prec spinor_prec,
 hisq_status hisq_autotune_dslash(hisq_gauge g, int n, hisq_prec spinor_prec,
                                  hisq_layout layout, int reps, int* rhs_per_thread,
                                  int* min_blocks, int* flags, double* seconds);
+
+/*
+ * Gauge load with an autotuned link compression (the paper compares the
+ * 18-real and 14-real Naik storage in Table 1 and Sec. 1; 12 reals for the
+ * fat links where exact): loads the links, exactly as hisq_gauge_load, with
+ * every (recon_U, recon_N) pair that has a kernel for `prec` (F64: 18/18;
+ * F32/F16: 18/18, 18/14, 12/14, 14/14), skips pairs that do not hold the
+ * links within recon_tol, runs hisq_autotune_dslash for n rhs in both spinor
+ * layouts on each, and returns in *out the handle whose SoA Dslash (the CG's
+ * layout) was fastest, with its tuned mappings. hisq_gauge_info reports the
+ * chosen compression. The choice is cached per (L, n, prec) for the life of
+ * the process; later calls load that pair directly (and search again if it
+ * does not hold their links). Transient device memory:
+ * two handles. Errors as hisq_gauge_load; HISQ_ERECON if no pair holds.
+ */
+hisq_status hisq_gauge_load_tuned(const int L[4], const void* U, const void* N, int on_device,
+                                  hisq_prec prec, int n, double recon_tol, void* stream,
+                                  hisq_gauge* out);
+
+/*
+ * Bundle-size search (Eq. 4 shares each link load among the n rhs of a
+ * bundle; Table 1 gives the arithmetic intensity as a function of n): times
+ * the autotuned Dslash for n = 1, 2, 4, ... <= n_max (n_max <= 16) and returns
+ * the bundle size with the lowest seconds per rhs and that time. The tuned
+ * mapping of every size tried stays cached on the handle.
+ */
+hisq_status hisq_autotune_bundle(hisq_gauge g, int n_max, hisq_prec prec, hisq_layout layout,
+                                 int reps, int* best_n, double* seconds_per_rhs);
 
 /*
  * Compress a canonical link field to `r` reals per link (R18/R14/R12, same

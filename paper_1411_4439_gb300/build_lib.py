@@ -30,15 +30,15 @@ NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler"
 
 # (object name, defines) of the Dslash families
 FAMILIES = [
-    ("dslash_f64_18_18", dict(HISQ_STORE="double", HISQ_RU=18, HISQ_RN=18, HISQ_MAX_RPT=4, HISQ_WITH_XY=1)),
-    ("dslash_f32_18_18", dict(HISQ_STORE="float", HISQ_RU=18, HISQ_RN=18, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
-    ("dslash_f32_18_14", dict(HISQ_STORE="float", HISQ_RU=18, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
-    ("dslash_f32_12_14", dict(HISQ_STORE="float", HISQ_RU=12, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
-    ("dslash_f32_14_14", dict(HISQ_STORE="float", HISQ_RU=14, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
-    ("dslash_f16_18_18", dict(HISQ_STORE="__half", HISQ_RU=18, HISQ_RN=18, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
-    ("dslash_f16_18_14", dict(HISQ_STORE="__half", HISQ_RU=18, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
-    ("dslash_f16_12_14", dict(HISQ_STORE="__half", HISQ_RU=12, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
-    ("dslash_f16_14_14", dict(HISQ_STORE="__half", HISQ_RU=14, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
+    ("dslash_f64_18_18", dict(HISQ_STORE="double", HISQ_LSTORE="double", HISQ_RU=18, HISQ_RN=18, HISQ_MAX_RPT=4, HISQ_WITH_XY=1)),
+    ("dslash_f32_18_18", dict(HISQ_STORE="float", HISQ_LSTORE="float", HISQ_RU=18, HISQ_RN=18, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
+    ("dslash_f32_18_14", dict(HISQ_STORE="float", HISQ_LSTORE="float", HISQ_RU=18, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
+    ("dslash_f32_12_14", dict(HISQ_STORE="float", HISQ_LSTORE="float", HISQ_RU=12, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
+    ("dslash_f32_14_14", dict(HISQ_STORE="float", HISQ_LSTORE="float", HISQ_RU=14, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
+    ("dslash_f16_18_18", dict(HISQ_STORE="__half", HISQ_LSTORE="hisq::Fx16", HISQ_RU=18, HISQ_RN=18, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
+    ("dslash_f16_18_14", dict(HISQ_STORE="__half", HISQ_LSTORE="hisq::Fx16", HISQ_RU=18, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
+    ("dslash_f16_12_14", dict(HISQ_STORE="__half", HISQ_LSTORE="hisq::Fx16", HISQ_RU=12, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
+    ("dslash_f16_14_14", dict(HISQ_STORE="__half", HISQ_LSTORE="hisq::Fx16", HISQ_RU=14, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
 ]
 PLAIN = ["hisq_api", "dslash_dispatch", "gauge", "blas", "force", "noalloc"]
 

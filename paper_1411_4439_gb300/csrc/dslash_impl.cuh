@@ -77,24 +77,24 @@ __device__ __forceinline__ void third_row(Link<RC>& m, const RC f) {
 template <typename LC, int RECON, typename RC>
 __device__ __forceinline__ void load_link(Link<RC>& m, const LC* __restrict__ base, int vh,
                                           int idx, typename Traits<float>::R inv_s_f,
-                                          double inv_s_d, int sign) {
+                                          double inv_s_d, int sign, const float* sc) {
     using R = decltype(RC{}.x);
     constexpr int NC = (RECON == 18) ? 9 : (RECON == 14 ? 7 : 6);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        const auto v = ld_stream(base + (size_t)c * vh + idx);
+        const auto v = link_elem(__ldcs(base + (size_t)c * vh + idx), sc[c]);
         m.e[c].x = (R)v.x;
         m.e[c].y = (R)v.y;
     }
     if (RECON == 18) {
 #pragma unroll
         for (int c = 6; c < 9; ++c) {
-            const auto v = ld_stream(base + (size_t)c * vh + idx);
+            const auto v = link_elem(__ldcs(base + (size_t)c * vh + idx), sc[c]);
             m.e[c].x = (R)v.x;
             m.e[c].y = (R)v.y;
         }
     } else if (RECON == 14) {
-        const auto zv = ld_stream(base + (size_t)(NC - 1) * vh + idx);
+        const auto zv = link_elem(__ldcs(base + (size_t)(NC - 1) * vh + idx), sc[NC - 1]);
         RC z;
         z.x = (R)zv.x;
         z.y = (R)zv.y;
@@ -358,14 +358,14 @@ __global__ void __launch_bounds__(256, MINB) dslash_kernel(const DslashArgs a) {
                 Link<RC> m;
                 if (hop == 0) {
                     const int sgn = (RU == 12 && mu == 3 && t == ext - 1) ? -eta : eta;
-                    load_link<LC, RU, RC>(m, Uf, vh, h, inv_s_f, a.r12_inv_scale, sgn);
+                    load_link<LC, RU, RC>(m, Uf, vh, h, inv_s_f, a.r12_inv_scale, sgn, a.lscale_u);
                 } else if (hop == 1) {
                     const int sgn = (RU == 12 && mu == 3 && t == 0) ? -eta : eta;
-                    load_link<LC, RU, RC>(m, Ubk, vh, hn, inv_s_f, a.r12_inv_scale, sgn);
+                    load_link<LC, RU, RC>(m, Ubk, vh, hn, inv_s_f, a.r12_inv_scale, sgn, a.lscale_u);
                 } else if (hop == 2) {
-                    load_link<LC, RN, RC>(m, Nf, vh, h, inv_s_f, a.r12_inv_scale, 1);
+                    load_link<LC, RN, RC>(m, Nf, vh, h, inv_s_f, a.r12_inv_scale, 1, a.lscale_n);
                 } else {
-                    load_link<LC, RN, RC>(m, Nbk, vh, hn, inv_s_f, a.r12_inv_scale, 1);
+                    load_link<LC, RN, RC>(m, Nbk, vh, hn, inv_s_f, a.r12_inv_scale, 1, a.lscale_n);
                 }
                 if (mu == 3 && a.has_mu) {
                     const double f = (hop == 0) ? a.ft1 : (hop == 1) ? a.bt1 : (hop == 2) ? a.ft3 : a.bt3;

@@ -1,7 +1,8 @@
 // One (storage precision, fat recon, Naik recon) family of Dslash kernels.
 //
 // This file is compiled once per family with
-//   -DHISQ_STORE=<double|float|__half> -DHISQ_RU=<18|12|14> -DHISQ_RN=<18|14>
+//   -DHISQ_STORE=<double|float|__half> -DHISQ_LSTORE=<double|float|hisq::Fx16>
+//   -DHISQ_RU=<18|12|14> -DHISQ_RN=<18|14>
 //   -DHISQ_FAMILY=<function name> -DHISQ_MAX_RPT=<4|8> -DHISQ_WITH_XY=<0|1>
 //   -DHISQ_LAYOUT=<0 (AoS)|1 (SoA)>
 // so the families build in parallel translation units. Each family holds the
@@ -13,7 +14,7 @@
 #include "dslash_pipe.cuh"
 #include "dslash_staged.cuh"
 
-#if !defined(HISQ_STORE) || !defined(HISQ_RU) || !defined(HISQ_RN) || !defined(HISQ_FAMILY) || \
+#if !defined(HISQ_STORE) || !defined(HISQ_LSTORE) || !defined(HISQ_RU) || !defined(HISQ_RN) || !defined(HISQ_FAMILY) || \
     !defined(HISQ_LAYOUT)
 #error "dslash_inst.cu needs HISQ_STORE, HISQ_RU, HISQ_RN, HISQ_FAMILY and HISQ_LAYOUT"
 #endif
@@ -21,14 +22,15 @@
 namespace hisq {
 
 #define HISQ_INST(R, B, P) \
-    launch_dslash_instance<S, S, HISQ_RU, HISQ_RN, R, B, EPI, LAYOUT, P>(a, s)
-#define HISQ_STAGED(R, B) launch_dslash_staged<S, S, HISQ_RU, HISQ_RN, R, B, EPI, LAYOUT>(a, s)
-#define HISQ_PIPE(R, B, D) launch_dslash_pipe<S, S, HISQ_RU, HISQ_RN, R, B, D, EPI, LAYOUT>(a, s)
+    launch_dslash_instance<S, LS, HISQ_RU, HISQ_RN, R, B, EPI, LAYOUT, P>(a, s)
+#define HISQ_STAGED(R, B) launch_dslash_staged<S, LS, HISQ_RU, HISQ_RN, R, B, EPI, LAYOUT>(a, s)
+#define HISQ_PIPE(R, B, D) launch_dslash_pipe<S, LS, HISQ_RU, HISQ_RN, R, B, D, EPI, LAYOUT>(a, s)
 
 template <int EPI, int LAYOUT>
 static cudaError_t family_by_variant(const DslashArgs& a, int rpt, int minb, int kind,
                                      cudaStream_t s) {
-    using S = HISQ_STORE;
+    using S = HISQ_STORE;       // spinor storage
+    using LS = HISQ_LSTORE;     // link storage
     const int key = rpt * 100 + minb * 10 + kind;
     switch (key) {
 #if HISQ_MAX_RPT >= 8

@@ -104,14 +104,15 @@ struct DslashPipe {
         constexpr bool NAIK = HOP >= 2;
         constexpr int REC = NAIK ? RN : RU;
         constexpr int NC = NAIK ? NCN : NCU;
+        const float* sc = NAIK ? a.lscale_n : a.lscale_u;
         Link<RC> m;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) m.e[c] = to_rc(b.l[c]);
+        for (int c = 0; c < 6; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
         if (REC == 18) {
 #pragma unroll
-            for (int c = 6; c < 9; ++c) m.e[c] = to_rc(b.l[c]);
+            for (int c = 6; c < 9; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
         } else if (REC == 14) {
-            third_row(m, to_rc(b.l[NC - 1]));
+            third_row(m, link_elem(b.l[NC - 1], sc[NC - 1]));
         } else {
             // staggered sign of this site's mu links; eta_mu(x - mu) = eta_mu(x),
             // and the antiperiodic t boundary flips the wrapped link

@@ -80,17 +80,17 @@ __device__ __forceinline__ int staged_offset(int lt) {
 // Link of `recon` reals from a shared stage run: component c at base[c * ts + idx].
 template <typename LC, int RECON, typename RC>
 __device__ __forceinline__ void load_link_shared(Link<RC>& m, const LC* base, int ts, int idx, float inv_s_f,
-                                                 double inv_s_d, int sign) {
+                                                 double inv_s_d, int sign, const float* sc) {
     using R = decltype(RC{}.x);
     constexpr int NC = (RECON == 18) ? 9 : (RECON == 14 ? 7 : 6);
 #pragma unroll
     for (int c = 0; c < (RECON == 18 ? 9 : 6); ++c) {
-        const auto v = to_float2_or_double2(base[c * ts + idx]);
+        const auto v = link_elem(base[c * ts + idx], sc[c]);
         m.e[c].x = (R)v.x;
         m.e[c].y = (R)v.y;
     }
     if (RECON == 14) {
-        const auto zv = to_float2_or_double2(base[(NC - 1) * ts + idx]);
+        const auto zv = link_elem(base[(NC - 1) * ts + idx], sc[NC - 1]);
         RC zz;
         zz.x = (R)zv.x;
         zz.y = (R)zv.y;
@@ -292,9 +292,9 @@ __global__ void __launch_bounds__(staged_max_threads(RPT), MINB) dslash_staged_k
                         if (hop == 0 && t == ext - 1) sgn = -eta;
                         if (hop == 1 && t == 0) sgn = -eta;
                     }
-                    load_link_shared<LC, RU, RC>(m, base, TS, sidx, inv_s_f, a.r12_inv_scale, sgn);
+                    load_link_shared<LC, RU, RC>(m, base, TS, sidx, inv_s_f, a.r12_inv_scale, sgn, a.lscale_u);
                 } else {
-                    load_link_shared<LC, RN, RC>(m, base, TS, sidx, inv_s_f, a.r12_inv_scale, 1);
+                    load_link_shared<LC, RN, RC>(m, base, TS, sidx, inv_s_f, a.r12_inv_scale, 1, a.lscale_n);
                 }
                 if (mu == 3 && a.has_mu) {
                     const double f = (hop == 0) ? a.ft1 : (hop == 1) ? a.bt1 : (hop == 2) ? a.ft3 : a.bt3;

@@ -2,7 +2,8 @@
 //
 // Canonical input: complex128 [4][V][3][3], lexicographic site order.
 // Internal output: [parity][mu][complex component][V_h] in the storage
-// precision, so that the Dslash reads each component of 32 consecutive
+// precision (FP64, FP32, or 16-bit fixed point with one scale per stored
+// component), so that the Dslash reads each component of 32 consecutive
 // sites with one coalesced warp access.
 //   R18: 9 components; R14: rows 1-2 and z with row3 = z conj(row1 x row2);
 //   R12: rows 1-2 with row3 = (sigma/s) conj(row1 x row2).
@@ -114,9 +115,28 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* bits, doub
     atomicMax(bits, (unsigned long long)__double_as_longlong(v));
 }
 
+// 16-bit fixed point: round to nearest of v / scale, clamped to +-32767
+__device__ __forceinline__ short quantize(double v, double inv_scale) {
+    double q = rint(v * inv_scale);
+    q = fmin(fmax(q, -32767.0), 32767.0);
+    return (short)q;
+}
+
+template <typename C>
+__device__ __forceinline__ C store_comp(double2 v, const double* comp_scale, int c) {
+    return narrow<C>(v);
+}
+template <>
+__device__ __forceinline__ short2 store_comp<short2>(double2 v, const double* comp_scale, int c) {
+    const double sc = comp_scale[c];
+    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+    return make_short2(quantize(v.x, inv), quantize(v.y, inv));
+}
+
 template <typename C>
 __global__ void pack_kernel(Geom g, const double2* __restrict__ canon, int recon, int hop,
-                            double inv_s, C* __restrict__ out, unsigned long long* err_bits) {
+                            double inv_s, C* __restrict__ out, unsigned long long* err_bits,
+                            const double* __restrict__ comp_scale) {
     const int nc = recon / 2;
     const long long V = 2ll * g.vh;
     double worst = 0.0;
@@ -131,9 +151,32 @@ __global__ void pack_kernel(Geom g, const double2* __restrict__ canon, int recon
         const int sg = (recon == 12) ? staggered_sign(g, s, mu, hop) : 1;
         worst = fmax(worst, encode(m, recon, sg, inv_s, enc));
         C* dst = out + ((size_t)(s.parity * 4 + mu) * nc) * g.vh + s.h;
-        for (int c = 0; c < nc; ++c) dst[(size_t)c * g.vh] = narrow<C>(enc[c]);
+        for (int c = 0; c < nc; ++c) dst[(size_t)c * g.vh] = store_comp<C>(enc[c], comp_scale, c);
     }
     if (err_bits != nullptr) atomic_max_nonneg(err_bits, worst);
+}
+
+__global__ void absmax_kernel(Geom g, const double2* __restrict__ canon, int recon, int hop,
+                              double inv_s, unsigned long long* maxbits) {
+    const int nc = recon / 2;
+    const long long V = 2ll * g.vh;
+    double mx[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) mx[c] = 0.0;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < 4 * V;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int mu = (int)(w / V);
+        const Site s = site_of(g, w - mu * V);
+        double2 m[9], enc[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) m[c] = canon[w * 9 + c];
+        const int sg = (recon == 12) ? staggered_sign(g, s, mu, hop) : 1;
+        encode(m, recon, sg, inv_s, enc);
+#pragma unroll
+        for (int c = 0; c < 9; ++c)
+            if (c < nc) mx[c] = fmax(mx[c], fmax(fabs(enc[c].x), fabs(enc[c].y)));
+    }
+    for (int c = 0; c < nc; ++c) atomic_max_nonneg(maxbits + c, mx[c]);
 }
 
 __global__ void compress_kernel(Geom g, const double2* __restrict__ canon, int recon, int hop,
@@ -197,23 +240,30 @@ unsigned grid_for(long long work) {
 
 cudaError_t launch_pack_links(const Geom& g, const double2* canon, int prec, int recon, int hop,
                               double r12_inv_scale, void* out, unsigned long long* err_bits,
-                              cudaStream_t s) {
+                              const double* comp_scale, cudaStream_t s) {
     const unsigned grid = grid_for(8ll * g.vh);
     switch (prec) {
         case HISQ_F64:
             pack_kernel<double2><<<grid, 256, 0, s>>>(g, canon, recon, hop, r12_inv_scale,
-                                                      (double2*)out, err_bits);
+                                                      (double2*)out, err_bits, comp_scale);
             break;
         case HISQ_F32:
             pack_kernel<float2><<<grid, 256, 0, s>>>(g, canon, recon, hop, r12_inv_scale,
-                                                     (float2*)out, err_bits);
+                                                     (float2*)out, err_bits, comp_scale);
             break;
         case HISQ_F16:
-            pack_kernel<__half2><<<grid, 256, 0, s>>>(g, canon, recon, hop, r12_inv_scale,
-                                                      (__half2*)out, err_bits);
+            if (comp_scale == nullptr) return cudaErrorInvalidValue;
+            pack_kernel<short2><<<grid, 256, 0, s>>>(g, canon, recon, hop, r12_inv_scale,
+                                                     (short2*)out, err_bits, comp_scale);
             break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_link_absmax(const Geom& g, const double2* canon, int recon, int hop,
+                               double r12_inv_scale, unsigned long long* maxbits, cudaStream_t s) {
+    absmax_kernel<<<grid_for(8ll * g.vh), 256, 0, s>>>(g, canon, recon, hop, r12_inv_scale, maxbits);
     return cudaGetLastError();
 }
 

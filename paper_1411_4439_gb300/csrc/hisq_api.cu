@@ -163,6 +163,8 @@ struct hisq_gauge_s {
     int device = 0;
     int prec = HISQ_F32, recon_U = 18, recon_N = 18;
     double r12_inv_scale = 1.0;
+    float lscale_u[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};   // 16-bit link component scales
+    float lscale_n[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
     void* U_lo = nullptr;        // storage copy (prec, recon)
     void* N_lo = nullptr;
     double2* U64 = nullptr;      // FP64 R18 copy
@@ -197,15 +199,39 @@ hisq_status pack_field(hisq_gauge g, const double2* canon, int prec, int recon, 
     const size_t sz = 2 * 4 * nc * (size_t)g->g.vh * prec_complex_bytes(prec);
     HISQ_CUDA(cudaMalloc(out, sz));
     *bytes += sz;
-    unsigned long long* err_bits = nullptr;
-    HISQ_CUDA(cudaMalloc(&err_bits, sizeof(unsigned long long)));
-    HISQ_CUDA(cudaMemsetAsync(err_bits, 0, sizeof(unsigned long long), s));
-    cudaError_t e = launch_pack_links(g->g, canon, prec, recon, hop, g->r12_inv_scale, *out,
-                                      err_bits, s);
+    // scratch: [0] reconstruct error bits, [1..9] component maxima (16-bit
+    // storage), then the 9 component scales as doubles
+    unsigned long long* scratch = nullptr;
+    HISQ_CUDA(cudaMalloc(&scratch, 19 * sizeof(unsigned long long)));
+    unsigned long long* err_bits = scratch;
+    double* comp_scale = reinterpret_cast<double*>(scratch + 10);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 19 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess && prec == HISQ_F16) {
+        // one scale per stored component: its largest |Re|, |Im| / 32767
+        e = launch_link_absmax(g->g, canon, recon, hop, g->r12_inv_scale, scratch + 1, s);
+        unsigned long long mb[9] = {0};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(mb, scratch + 1, sizeof(mb), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        double sc[9];
+        float* keep = (hop == 1) ? g->lscale_u : g->lscale_n;
+        for (size_t c = 0; c < 9; ++c) {
+            double mx;
+            memcpy(&mx, &mb[c], sizeof(mx));
+            sc[c] = (c < nc && mx > 0.0 && std::isfinite(mx)) ? mx / 32767.0 : 1.0;
+            // the kernels dequantise with the FP32 scale: quantise with the same value
+            keep[c] = (float)sc[c];
+            sc[c] = (double)keep[c];
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(comp_scale, sc, sizeof(sc), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e == cudaSuccess)
+        e = launch_pack_links(g->g, canon, prec, recon, hop, g->r12_inv_scale, *out, err_bits,
+                              prec == HISQ_F16 ? comp_scale : nullptr, s);
     unsigned long long bits = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, err_bits, sizeof(bits), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(err_bits);
+    cudaFree(scratch);
     HISQ_CUDA(e);
     double err;
     memcpy(&err, &bits, sizeof(err));
@@ -419,6 +445,9 @@ int auto_rpt(int n, int prec) {
     const int mx = dslash_max_rpt(prec);
     int r = 1;
     while (r * 2 <= mx && n % (r * 2) == 0) r *= 2;
+    // FP32/FP16 storage below 16 rhs: two groups of four rhs per thread with
+    // the pipelined kernel beat one group of eight
+    if (prec != HISQ_F64 && r == 8 && n < 16) r = 4;
     while (n / r > 8 && r < mx) r *= 2;   // at most 8 rhs groups per block
     return r;
 }
@@ -495,6 +524,10 @@ void fill_common(DslashArgs& a, hisq_gauge g, int prec, int parity, int n) {
     a.ft1 = a.bt1 = a.ft3 = a.bt3 = 1.0;
     a.has_mu = 0;
     a.r12_inv_scale = g->r12_inv_scale;
+    for (int c = 0; c < 9; ++c) {
+        a.lscale_u[c] = g->lscale_u[c];
+        a.lscale_n[c] = g->lscale_n[c];
+    }
     a.red_mode = RED_NONE;
     a.finish = FIN_STORE;
 }
@@ -681,6 +714,109 @@ extern "C" hisq_status hisq_autotune_dslash(hisq_gauge g, int n, hisq_prec prec,
     if (minb) *minb = best_t.minb;
     if (flags) *flags = flags_of_tune(best_t);
     if (seconds) *seconds = best;
+    return HISQ_OK;
+}
+
+// Gauge load that also chooses the link compression: every (recon_U, recon_N)
+// pair with a kernel for the storage precision and exact for these links is
+// loaded and autotuned for n rhs; the fastest handle is kept. Choices are
+// cached per (L, n, prec) for the process.
+namespace {
+
+struct TunedShape {
+    int ru, rn;
+    std::map<int, DslashTune> tuned;
+};
+std::mutex g_shape_mtx;
+std::map<std::tuple<int, int, int, int, int, int>, TunedShape> g_shape_cache;
+
+}  // namespace
+
+extern "C" hisq_status hisq_gauge_load_tuned(const int L[4], const void* U, const void* N, int on_device,
+                                            hisq_prec prec, int n, double recon_tol, void* stream,
+                                            hisq_gauge* out) {
+    if (out == nullptr) return fail(HISQ_EINVAL, "out handle pointer is NULL");
+    *out = nullptr;
+    if (L == nullptr) return fail(HISQ_EINVAL, "L is NULL");
+    if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
+    if (!valid_prec(prec)) return fail(HISQ_EINVAL, "unknown precision %d", prec);
+    const auto key = std::make_tuple(L[0], L[1], L[2], L[3], n, (int)prec);
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mtx);
+        auto it = g_shape_cache.find(key);
+        if (it != g_shape_cache.end()) {
+            hisq_status st = hisq_gauge_load(L, U, N, on_device, prec, (hisq_recon)it->second.ru,
+                                             (hisq_recon)it->second.rn, recon_tol, stream, out);
+            if (st == HISQ_OK) (*out)->tuned = it->second.tuned;
+            // links of the same shape that the cached pair cannot hold: search again
+            if (st != HISQ_ERECON) return st;
+        }
+    }
+    std::vector<std::pair<int, int>> pairs;
+    if (prec == HISQ_F64)
+        pairs = {{18, 18}};
+    else
+        pairs = {{18, 18}, {18, 14}, {12, 14}, {14, 14}};
+    hisq_gauge best = nullptr;
+    double best_s = HUGE_VAL;
+    hisq_status last = HISQ_OK;
+    for (const auto& pr : pairs) {
+        hisq_gauge g = nullptr;
+        hisq_status st = hisq_gauge_load(L, U, N, on_device, prec, (hisq_recon)pr.first, (hisq_recon)pr.second,
+                                         recon_tol, stream, &g);
+        if (st == HISQ_ERECON) continue;        // not exact for these links
+        if (st != HISQ_OK) {
+            last = st;
+            break;
+        }
+        double sec_soa = 0.0, sec_aos = 0.0;
+        st = hisq_autotune_dslash(g, n, prec, HISQ_SOA, 5, nullptr, nullptr, nullptr, &sec_soa);
+        if (st == HISQ_OK) st = hisq_autotune_dslash(g, n, prec, HISQ_AOS, 5, nullptr, nullptr, nullptr, &sec_aos);
+        if (st != HISQ_OK) {
+            hisq_gauge_free(g);
+            last = st;
+            break;
+        }
+        if (sec_soa < best_s) {
+            if (best) hisq_gauge_free(best);
+            best = g;
+            best_s = sec_soa;
+        } else {
+            hisq_gauge_free(g);
+        }
+    }
+    if (last != HISQ_OK) {
+        if (best) hisq_gauge_free(best);
+        return last;
+    }
+    if (!best) return fail(HISQ_ERECON, "no link compression holds these links within recon_tol");
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mtx);
+        g_shape_cache[key] = TunedShape{best->recon_U, best->recon_N, best->tuned};
+    }
+    *out = best;
+    return HISQ_OK;
+}
+
+// Bundle size: seconds per rhs of the tuned Dslash for every power-of-two
+// bundle up to n_max; the smallest wins.
+extern "C" hisq_status hisq_autotune_bundle(hisq_gauge g, int n_max, hisq_prec prec, hisq_layout layout,
+                                           int reps, int* best_n, double* seconds_per_rhs) {
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    if (n_max < 1 || n_max > kMaxRhs) return fail(HISQ_EINVAL, "n_max = %d outside 1..%d", n_max, kMaxRhs);
+    int bn = 0;
+    double bs = HUGE_VAL;
+    for (int n = 1; n <= n_max; n *= 2) {
+        double sec = 0.0;
+        hisq_status st = hisq_autotune_dslash(g, n, prec, layout, reps, nullptr, nullptr, nullptr, &sec);
+        if (st != HISQ_OK) return st;
+        if (sec / n < bs) {
+            bs = sec / n;
+            bn = n;
+        }
+    }
+    if (best_n) *best_n = bn;
+    if (seconds_per_rhs) *seconds_per_rhs = bs;
     return HISQ_OK;
 }
 

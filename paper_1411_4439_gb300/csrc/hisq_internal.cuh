@@ -54,6 +54,28 @@ template <> struct Traits<__half> {
     static constexpr int prec = HISQ_F16;
 };
 
+// 16-bit link storage: each real is a signed 16-bit integer q with value
+// q * scale_c, one scale per stored complex component c of a field (the
+// largest |Re|, |Im| of that component over the field / 32767). Links have a
+// known bounded range, so this keeps 2^-15 of the range where IEEE half keeps
+// 2^-11 of each value.
+struct Fx16 {};
+template <> struct Traits<Fx16> {
+    using C = short2;
+    using R = float;
+    using RC = float2;
+    static constexpr int prec = HISQ_F16;
+};
+
+// One stored link component in arithmetic precision; sc is the component's
+// scale (used by the 16-bit fixed-point storage only).
+__device__ __forceinline__ double2 link_elem(double2 v, float) { return v; }
+__device__ __forceinline__ float2 link_elem(float2 v, float) { return v; }
+__device__ __forceinline__ float2 link_elem(__half2 v, float) { return __half22float2(v); }
+__device__ __forceinline__ float2 link_elem(short2 v, float sc) {
+    return make_float2((float)v.x * sc, (float)v.y * sc);
+}
+
 __device__ __forceinline__ double2 ld_c(const double2* p) { return __ldg(p); }
 __device__ __forceinline__ float2 ld_c(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ float2 ld_c(const __half2* p) { return __half22float2(__ldg(p)); }
@@ -148,6 +170,8 @@ struct DslashArgs {
     int l2_prefetch;                    // 1: bulk-prefetch each tile's links into L2
     int* status;                        // bounded waits that give up OR kFlagTimeout here (or null)
     double r12_inv_scale;               // 1 / s for R12 fat links
+    float lscale_u[9];                  // per-component scales of 16-bit fat links
+    float lscale_n[9];                  // per-component scales of 16-bit Naik links
     int red_mode;
     int finish;
     double tol2;                        // FIN_RELIABLE: tol^2
@@ -181,6 +205,7 @@ bool dslash_variant_supported(int prec, int ru, int rn, int epi);
 // Built (rpt, minb, kind) mappings of a precision, and the default one for an rpt.
 bool dslash_mapping_built(int prec, int rpt, int minb, int kind);
 DslashTune dslash_default_tune(int prec, int rpt, int layout);
+DslashTune dslash_register_tune(int prec, int rpt, int layout);
 // Whether the staged-link kernel can run this lattice with `groups` groups of rpt rhs.
 bool dslash_staged_ok(const Geom& g, int prec, int rpt, int groups);
 // Largest rhs-per-thread value instantiated for a precision.
@@ -196,9 +221,16 @@ cudaError_t launch_transpose_spinor(const double2* in, double2* out, int n, int 
 // ---------------------------------------------------------------------------
 // Pack canonical complex128 [4][V][3][3] into [2][4][ncomp][vh] of `prec`,
 // with reconstruct residual max written (as ordered bits) to *err_bits.
+// F16 links are 16-bit fixed point: comp_scale[c] (device, FP64) is the
+// scale of stored component c (see launch_link_absmax); ignored otherwise.
 cudaError_t launch_pack_links(const Geom& g, const double2* canon, int prec, int recon,
                               int hop, double r12_inv_scale, void* out,
-                              unsigned long long* err_bits, cudaStream_t s);
+                              unsigned long long* err_bits, const double* comp_scale,
+                              cudaStream_t s);
+// Largest |Re| or |Im| of every stored component (recon / 2 of them) over the
+// field, as the bits of non-negative doubles OR-maximised into maxbits[c].
+cudaError_t launch_link_absmax(const Geom& g, const double2* canon, int recon, int hop,
+                               double r12_inv_scale, unsigned long long* maxbits, cudaStream_t s);
 // Compress to double [4][V][r] and back (ABI helpers).
 cudaError_t launch_compress_links(const Geom& g, const double2* canon, int recon, int hop,
                                   double r12_inv_scale, double* packed,

@@ -41,7 +41,7 @@ HISQ_MAP_PIPELINED, HISQ_MAP_PIPELINED2 = 8, 16
 
 EXPORTED = ["hisq_version", "hisq_last_error", "hisq_gauge_load", "hisq_gauge_free",
             "hisq_gauge_info", "hisq_set_dslash_mapping", "hisq_get_dslash_mapping",
-            "hisq_autotune_dslash",
+            "hisq_autotune_dslash", "hisq_gauge_load_tuned", "hisq_autotune_bundle",
             "hisq_link_compress",
             "hisq_link_reconstruct", "hisq_dslash", "hisq_dslash_ex", "hisq_mdagm",
             "hisq_apply_m", "hisq_link_force", "hisq_cdot", "hisq_cdot_noalloc",
@@ -99,6 +99,8 @@ def library() -> ctypes.CDLL:
         "hisq_get_dslash_mapping": (c_int, [vp, c_int, c_int, ip, ip, ip]),
         "hisq_autotune_dslash": (c_int, [vp, c_int, c_int, c_int, c_int, ip, ip, ip,
                                          ctypes.POINTER(c_double)]),
+        "hisq_gauge_load_tuned": (c_int, [ip, vp, vp, c_int, c_int, c_int, c_double, vp, ctypes.POINTER(vp)]),
+        "hisq_autotune_bundle": (c_int, [vp, c_int, c_int, c_int, c_int, ip, ctypes.POINTER(c_double)]),
         "hisq_link_compress": (c_int, [ip, vp, c_int, vp, ctypes.POINTER(c_double), vp]),
         "hisq_link_reconstruct": (c_int, [ip, vp, c_int, vp, vp]),
         "hisq_dslash": (c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int, c_int, vp]),
@@ -238,6 +240,20 @@ def hisq_gauge_load(L, U, N, prec=HISQ_F32, recon_U=HISQ_R18, recon_N=HISQ_R18,
     return Gauge(h.value, tuple(int(a) for a in L), int(prec), int(recon_U), int(recon_N))
 
 
+def hisq_gauge_load_tuned(L, U, N, prec=HISQ_F32, n=8, recon_tol=1e-10, stream=None) -> Gauge:
+    """Load the links with the compression pair whose tuned Dslash for n rhs is fastest."""
+    on_dev = _is_device(U)
+    if on_dev != _is_device(N):
+        raise ValueError("U and N must both be on the device or both on the host")
+    h = ctypes.c_void_p()
+    _check(library().hisq_gauge_load_tuned(_lattice(L), _ptr(U), _ptr(N), int(on_dev), int(prec), int(n),
+                                           float(recon_tol), _stream_handle(stream, U, N), ctypes.byref(h)))
+    g = Gauge(h.value, tuple(int(a) for a in L), int(prec), 0, 0)
+    info = hisq_gauge_info(g)
+    g.recon_U, g.recon_N = info["recon_U"], info["recon_N"]
+    return g
+
+
 def hisq_gauge_free(g: Gauge) -> None:
     if g is None or g._freed:
         return
@@ -279,6 +295,14 @@ def hisq_autotune_dslash(g: Gauge, n: int, prec: int, layout: int = HISQ_SOA, re
                                           ctypes.byref(r), ctypes.byref(b), ctypes.byref(f),
                                           ctypes.byref(sec)))
     return dict(rhs_per_thread=r.value, min_blocks=b.value, flags=f.value, seconds=sec.value)
+
+
+def hisq_autotune_bundle(g: Gauge, n_max: int, prec: int, layout: int = HISQ_SOA, reps: int = 5) -> dict:
+    """Bundle size (power of two <= n_max) with the lowest tuned Dslash time per rhs."""
+    bn, sec = ctypes.c_int(), ctypes.c_double()
+    _check(library().hisq_autotune_bundle(g.handle, int(n_max), int(prec), int(layout), int(reps),
+                                          ctypes.byref(bn), ctypes.byref(sec)))
+    return dict(n=bn.value, seconds_per_rhs=sec.value)
 
 
 def hisq_link_compress(L, links, recon, packed, stream=None) -> float:

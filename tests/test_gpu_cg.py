@@ -289,3 +289,19 @@ def test_batched_rejects_shared_handle(gpu_lib):
         assert ei.value.status == H.hisq.HISQ_EINVAL
     finally:
         H.hisq_gauge_free(g)
+
+
+def test_fp16_storage_converges_at_light_mass(gpu_lib):
+    """m = 0.0025 (A's condition number ~ 1e6): with 16-bit fixed-point links the
+    FP16-storage solve converges like the FP32 one and meets the oracle's residual."""
+    H = gpu_lib
+    L, m, n = (8, 8, 8, 8), 0.0025, 2
+    U, N = gen.hisq_links(L, seed=1)
+    b = gen.gaussian_source(L, n, seed=2)
+    x16, st16 = solve(H, L, U, N, b, m, prec=2, ru=18, rn=14, maxiter=40000)
+    x32, st32 = solve(H, L, U, N, b, m, prec=1, ru=18, rn=14, maxiter=40000)
+    A = lambda q: O.apply_Ae(U, N, q, L, m)
+    res = O.true_relative_residual(A, x16, b)
+    assert np.all(res <= 1e-10), res
+    assert st16.total_iters <= 1.3 * st32.total_iters, (st16.total_iters, st32.total_iters)
+    assert rel_l2(x16, x32) <= 1e-7

@@ -433,3 +433,49 @@ def test_pipelined_mapping_in_solve_and_mu_derivative(gpu_lib):
         H.hisq_gauge_free(g)
     res = O.true_relative_residual(lambda q: O.apply_Ae(U, N, q, L, m), x, b)
     assert np.all(res <= 1e-10)
+
+
+def test_tuned_gauge_load_picks_an_exact_compression(gpu_lib):
+    """The compression tuner only keeps pairs that hold the links; its handle
+    computes the oracle's Dslash and the choice is cached for the shape."""
+    import torch
+    H = gpu_lib
+    L = (16, 16, 4, 6)
+    U, N = links(L)
+    n = 8
+    dU, dN = torch.from_numpy(U).cuda(), torch.from_numpy(N).cuda()
+    g = H.hisq_gauge_load_tuned(L, dU, dN, prec=1, n=n)
+    try:
+        assert (g.recon_U, g.recon_N) in ((18, 18), (18, 14), (12, 14), (14, 14))
+        v = gen.gaussian_source(L, n, seed=95)
+        vd = [to_dev(v[k], 1) for k in range(n)]
+        wd = [torch.empty_like(t) for t in vd]
+        H.hisq_dslash(g, vd, wd, 0, 1)
+        torch.cuda.synchronize()
+        ref = O.dslash_parity(U, N, v, L, 0)
+        for k in range(n):
+            assert rel_l2(from_dev(wd[k]), ref[k]) < 1e-6
+        g2 = H.hisq_gauge_load_tuned(L, dU, dN, prec=1, n=n)
+        try:
+            assert (g2.recon_U, g2.recon_N) == (g.recon_U, g.recon_N)
+        finally:
+            H.hisq_gauge_free(g2)
+        best = H.hisq_autotune_bundle(g, 8, 1)
+        assert best["n"] in (1, 2, 4, 8) and best["seconds_per_rhs"] > 0
+    finally:
+        H.hisq_gauge_free(g)
+    # fat links 0.9 x U(3) (not SU(3)): R12 cannot hold them, the tuner must skip it
+    Ualt = (-0.9 * 24.0) * N
+    g = H.hisq_gauge_load_tuned((16, 16, 4, 6), torch.from_numpy(Ualt).cuda(), dN, prec=1, n=4)
+    try:
+        assert g.recon_U != 12
+        v = gen.gaussian_source(L, 4, seed=96)
+        vd = [to_dev(v[k], 1) for k in range(4)]
+        wd = [torch.empty_like(t) for t in vd]
+        H.hisq_dslash(g, vd, wd, 1, 1)
+        torch.cuda.synchronize()
+        ref = O.dslash_parity(Ualt, N, v, L, 1)
+        for k in range(4):
+            assert rel_l2(from_dev(wd[k]), ref[k]) < 1e-6
+    finally:
+        H.hisq_gauge_free(g)
