@@ -165,7 +165,7 @@ class ClockSampler:
 # one ncu capture of that kernel (profiles/dslash_f32_r18_r14_n8_32x32x32x8_pipelined.md),
 # keyed by (lattice, rhs per thread, min blocks, mapping flags). A mapping
 # without a capture reports null.
-DSLASH_TRAFFIC = {((32, 32, 32, 8), 4, 2, 16): 159_459_072 + 5_535_744}
+DSLASH_TRAFFIC = {((32, 32, 32, 8), 4, 2, 16): 159_460_352 + 5_904_896}
 
 
 def dslash_kernel_name(rpt, minb, flags, L):
@@ -274,7 +274,10 @@ def run_gpu(args):
         e1.record(stream)
         e1.synchronize()
         durs.append(e0.elapsed_time(e1) / 1e3)
-        launches += 4 * st.total_iters + 4 * st.reliable_updates + 3
+        # per iteration: two Dslash, update_r, update_px; per reliable update:
+        # accumulate, two FP64 Dslash, rescale; per solve: transpose b into the
+        # SoA workspace, norm |b|, copy the residual, rescale, transpose x out
+        launches += 4 * st.total_iters + 4 * st.reliable_updates + 5
         stats_last = st
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
@@ -396,9 +399,115 @@ def run_gpu(args):
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
 
+def _oracle_cg_iteration_seconds(apply_A, b, iters: int) -> float:
+    from oracle import hisq_oracle as O
+    t0 = time.perf_counter()
+    O.cg(apply_A, b, tol=1e-300, maxiter=iters)
+    return (time.perf_counter() - t0) / iters
+
+
+_WORKER = {}
+
+
+def _oracle_worker_init(Ls):
+    """Links and sources of the all-core sample, built once per spawned process."""
+    import hisq_inputs as gen
+    _WORKER["L"] = Ls
+    _WORKER["links"] = gen.hisq_links(Ls, seed=LINK_SEED)
+    _WORKER["b"] = gen.z2_source(Ls, NRHS, seed=SOURCE_SEED)
+
+
+def _oracle_sample_worker(job):
+    """CG iterations of one rhs of the all-core sample (in a spawned process)."""
+    from oracle import hisq_oracle as O
+    mass, k, iters = job
+    U, N = _WORKER["links"]
+    Ls = _WORKER["L"]
+    t0 = time.perf_counter()
+    O.cg(lambda q: O.apply_Ae(U, N, q, Ls, mass), _WORKER["b"][k:k + 1], tol=1e-300, maxiter=iters)
+    return time.perf_counter() - t0
+
+
+def run_oracle_timing(args):
+    """The FP64 oracle on the host cores for every configuration: one Dslash
+    call, and CG seconds per rhs (to convergence on 8^4; elsewhere a bounded
+    sample of iterations scaled by the iteration count of that system). The
+    all-core line runs the 8 rhs of the 32^3x8 bundle as 8 spawned processes."""
+    import multiprocessing as mp
+
+    import hisq_inputs as gen
+    from oracle import hisq_oracle as O
+    cpus = os.cpu_count() or 1
+
+    def line(d):
+        d.update({"impl": "reference", "kind": "oracle", "host_cpus": cpus})
+        print(json.dumps(d), flush=True)
+
+    def dslash_s(U, N, v, Ls):
+        t0 = time.perf_counter()
+        O.dslash_parity(U, N, v, Ls, 0)
+        return time.perf_counter() - t0
+
+    # configs[0]: 8^4, FP64, one rhs, m = 0.05, to convergence
+    L0 = (8, 8, 8, 8)
+    U, N = gen.hisq_links(L0, seed=0)
+    b = gen.z2_source(L0, 1, seed=0)
+    t0 = time.perf_counter()
+    _, it = O.cg(lambda q: O.apply_Ae(U, N, q, L0, 0.05), b, tol=TOL)
+    line({"workload": "oracle 8^4 m=0.05", "cores": 1, "cg_s_per_rhs": time.perf_counter() - t0,
+          "cg_iterations": int(it[0]), "dslash_s_per_call_1rhs": dslash_s(U, N, b, L0),
+          "sample": "complete solve"})
+
+    # configs[1]: 32^3x8, m = 0.01
+    U, N = gen.hisq_links(L, seed=LINK_SEED)
+    b = gen.z2_source(L, NRHS, seed=SOURCE_SEED)
+    iters_total, how = fp64_iterations(None)
+    t_it = _oracle_cg_iteration_seconds(lambda q: O.apply_Ae(U, N, q, L, MASS), b[:1], 2)
+    line({"workload": "oracle 32^3x8 m=0.01", "cores": 1, "cg_s_per_rhs": t_it * iters_total,
+          "cg_iterations": iters_total, "iterations_from": how,
+          "dslash_s_per_call_8rhs": dslash_s(U, N, b, L),
+          "sample": f"2 CG iterations of one rhs ({t_it:.3f} s/iteration)"})
+    procs = min(NRHS, cpus)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs, initializer=_oracle_worker_init, initargs=(L,)) as pool:
+        pool.map(_oracle_sample_worker, [(MASS, 0, 1)] * procs, chunksize=1)     # warm-up
+        t0 = time.perf_counter()
+        pool.map(_oracle_sample_worker, [(MASS, k, 2) for k in range(NRHS)], chunksize=1)
+        wall = time.perf_counter() - t0
+    per_it_bundle = wall / 2
+    line({"workload": "oracle 32^3x8 m=0.01, all cores", "cores": procs,
+          "cg_s_per_rhs": per_it_bundle * iters_total / NRHS, "cg_iterations": iters_total,
+          "sample": f"2 CG iterations of each of the {NRHS} rhs in {procs} spawned processes"})
+    del U, N, b
+
+    # configs[2]: 48^3x12, m = 0.0025, Gaussian; iteration count of the GPU FP64 solve
+    L2 = (48, 48, 48, 12)
+    U, N = gen.hisq_links(L2, seed=LINK_SEED)
+    b = gen.gaussian_source(L2, 1, seed=SOURCE_SEED)
+    t_it = _oracle_cg_iteration_seconds(lambda q: O.apply_Ae(U, N, q, L2, 0.0025), b, 1)
+    line({"workload": "oracle 48^3x12 m=0.0025", "cores": 1, "cg_s_per_rhs": t_it * 11310,
+          "cg_iterations": 11310, "iterations_from": "FP64 GPU solve of the same system",
+          "dslash_s_per_call_1rhs": dslash_s(U, N, b, L2),
+          "sample": f"1 CG iteration of one rhs ({t_it:.2f} s/iteration)"})
+    del U, N, b
+
+    # configs[3]: 16^4, mu = 0.1, full lattice M^dag M, m = 0.05
+    L3 = (16, 16, 16, 16)
+    U, N = gen.hisq_links(L3, seed=LINK_SEED)
+    v = O.to_full(gen.z2_source(L3, 1, seed=SOURCE_SEED), L3, 0) + \
+        O.to_full(gen.z2_source(L3, 1, seed=SOURCE_SEED + 7), L3, 1)
+    t_it = _oracle_cg_iteration_seconds(lambda q: O.apply_MdagM(U, N, q, 0.05, 0.1), v, 2)
+    line({"workload": "oracle 16^4 mu=0.1 full lattice", "cores": 1, "cg_s_per_rhs": t_it * 930,
+          "cg_iterations": 930, "iterations_from": "FP64 GPU solve of the same system",
+          "sample": f"2 CG iterations of one rhs ({t_it:.3f} s/iteration)"})
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload == "oracle-timing":
+        run_oracle_timing(args)
         return
     import hisq_inputs as gen
     U, N = gen.hisq_links(L, seed=LINK_SEED)
@@ -651,14 +760,64 @@ def run_batched(args):
         H.hisq_gauge_free(g)
 
 
+def run_inverter_sweep(args):
+    """Inverter GFlop/s with 4 rhs against lattice size (the paper's Fig. 4,
+    right): 300 CG iterations of the FP32-inner even-odd solve at m = 0.01
+    on each lattice, flops 2 x 1146 + 12 (mass term) + 60 (vector updates) per
+    even site, rhs and iteration, reliable updates included in the time."""
+    import torch
+
+    import hisq_inputs as gen
+    import paper_1411_4439_gb300 as H
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    H.hisq.library()
+    n, iters = 4, 300
+    for Ls in ((16, 16, 16, 16), (24, 24, 24, 6), (32, 32, 32, 8), (48, 48, 48, 12), (64, 64, 64, 16)):
+        U, N = gen.hisq_links(Ls, seed=LINK_SEED)
+        g = H.hisq_gauge_load(Ls, torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev),
+                              prec=H.HISQ_F32, recon_U=18, recon_N=14)
+        del U, N
+        b = gen.z2_source(Ls, n, seed=SOURCE_SEED)
+        bt = [torch.from_numpy(b[k]).to(dev) for k in range(n)]
+        xt = [torch.zeros_like(t) for t in bt]
+        p = H.cg_params(inner_prec=H.HISQ_F32, reliable_every=RELIABLE_EVERY, maxiter=iters)
+
+        def solve():
+            try:
+                return H.hisq_cg_solve(g, MASS, 0.0, bt, xt, 1e-30, p, stream=stream)
+            except H.HisqError as e:          # HISQ_ENOCONV at maxiter: stats ride on the error
+                return e.stats
+        solve()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = solve()
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        vh = int(np.prod(Ls)) // 2
+        flops = (2 * DSLASH_FLOPS_PER_SITE_RHS + 12 + 60) * vh * n * st.total_iters
+        print(json.dumps({"workload": "inverter sweep, n=4, FP32 inner", "lattice": list(Ls),
+                          "iterations": st.total_iters, "reliable_updates": st.reliable_updates,
+                          "s": t, "gflops": round(flops / t / 1e9, 1),
+                          "us_per_iteration": round(t / st.total_iters * 1e6, 1)}), flush=True)
+        H.hisq_gauge_free(g)
+        del bt, xt
+        torch.cuda.empty_cache()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["headline", "cg-configs", "dslash-sweep", "batched"],
-                    default="headline", help="headline = the one JSON line of the contract")
+    ap.add_argument("--workload", choices=["headline", "cg-configs", "dslash-sweep", "batched", "inverter-sweep",
+                                           "oracle-timing"],
+                    default="headline",
+                    help="headline = the one JSON line of the contract; oracle-timing needs --impl reference")
     ap.add_argument("--lattices", default="48x48x48x12,64x64x64x16",
                     help="lattices of the Dslash sweep (Lx x Ly x Lz x Lt, comma separated)")
     args = ap.parse_args(argv)
@@ -671,6 +830,8 @@ def main(argv=None):
         run_dslash_sweep(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "inverter-sweep":
+        run_inverter_sweep(args)
     else:
         run_gpu(args)
 

@@ -146,14 +146,13 @@ template <int N> struct XVec<double, N> {
     }
 };
 
-// x += alpha p ; r -= alpha Ap ; rr' = |r|^2 ; finish: beta = rr'/rr
+// r -= alpha Ap ; rr' = |r|^2 of the stored residual ; finish: beta = rr'/rr.
+// The solution update waits for update_px, which reads p before it changes.
 template <typename S>
-__global__ void __launch_bounds__(kThreads) update_xr_kernel(BlasArgs a, void* x, void* r,
-                                                             const void* p, const void* Ap) {
+__global__ void __launch_bounds__(kThreads) update_r_kernel(BlasArgs a, void* r, const void* Ap) {
     using V = Vec<S>;
     using R = typename V::R;
     using RC = typename CxOf<R>::T;
-    using X = XVec<typename XType<S>::T, V::N>;
     constexpr int N = V::N;
     const int k = blockIdx.y;
     const long long nch = a.len / N;
@@ -163,19 +162,14 @@ __global__ void __launch_bounds__(kThreads) update_xr_kernel(BlasArgs a, void* x
         const R alpha = (R)a.cg->alpha[k];
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nch;
              i += (long long)gridDim.x * blockDim.x) {
-            RC xv[N], rv[N], pv[N], av[N];
-            X::load(x, off + i, xv);
+            RC rv[N], av[N];
             V::load(r, off + i, rv);
-            V::load(p, off + i, pv);
             V::load(Ap, off + i, av);
 #pragma unroll
             for (int c = 0; c < N; ++c) {
-                xv[c].x = fma(alpha, pv[c].x, xv[c].x);
-                xv[c].y = fma(alpha, pv[c].y, xv[c].y);
                 rv[c].x = fma(-alpha, av[c].x, rv[c].x);
                 rv[c].y = fma(-alpha, av[c].y, rv[c].y);
             }
-            X::store(x, off + i, xv);
             V::store(r, off + i, rv);
             V::round(rv);   // the norm is that of the stored residual
 #pragma unroll
@@ -187,29 +181,48 @@ __global__ void __launch_bounds__(kThreads) update_xr_kernel(BlasArgs a, void* x
     if (block_reduce_arrive<R, 1>(a.red, val, a.n, mx, s_vals)) finish_cg_beta(a.cg, s_vals, a.n);
 }
 
-// p = r + beta p
+// x += alpha p ; p = r + beta p, both from the old p, in one pass. alpha is
+// zero for an rhs that did not move this iteration; an rhs frozen by this
+// iteration's finish still takes its x update but keeps p.
 template <typename S>
-__global__ void __launch_bounds__(kThreads) update_p_kernel(BlasArgs a, const void* r, void* p) {
+__global__ void __launch_bounds__(kThreads) update_px_kernel(BlasArgs a, void* x, const void* r, void* p) {
     using V = Vec<S>;
     using R = typename V::R;
     using RC = typename CxOf<R>::T;
+    using X = XVec<typename XType<S>::T, V::N>;
     constexpr int N = V::N;
     const int k = blockIdx.y;
-    if (!moving(a.cg, k)) return;
+    const R alpha = (R)a.cg->alpha[k];
+    const bool move = moving(a.cg, k);
+    const bool upd_x = alpha != (R)0;
+    if (!move && !upd_x) return;
     const long long nch = a.len / N;
     const long long off = (long long)k * nch;
     const R beta = (R)a.cg->beta[k];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nch;
          i += (long long)gridDim.x * blockDim.x) {
-        RC rv[N], pv[N];
-        V::load(r, off + i, rv);
+        RC pv[N];
         V::load(p, off + i, pv);
+        if (upd_x) {
+            RC xv[N];
+            X::load(x, off + i, xv);
 #pragma unroll
-        for (int c = 0; c < N; ++c) {
-            pv[c].x = fma(beta, pv[c].x, rv[c].x);
-            pv[c].y = fma(beta, pv[c].y, rv[c].y);
+            for (int c = 0; c < N; ++c) {
+                xv[c].x = fma(alpha, pv[c].x, xv[c].x);
+                xv[c].y = fma(alpha, pv[c].y, xv[c].y);
+            }
+            X::store(x, off + i, xv);
         }
-        V::store(p, off + i, pv);
+        if (move) {
+            RC rv[N];
+            V::load(r, off + i, rv);
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                pv[c].x = fma(beta, pv[c].x, rv[c].x);
+                pv[c].y = fma(beta, pv[c].y, rv[c].y);
+            }
+            V::store(p, off + i, pv);
+        }
     }
 }
 
@@ -449,16 +462,16 @@ constexpr int vec_n() {
         default: return cudaErrorInvalidValue;        \
     }
 
-cudaError_t launch_cg_update_xr(const BlasArgs& a, int prec, void* x, void* r, const void* p,
-                                const void* Ap, cudaStream_t s) {
-    HISQ_PREC_SWITCH(prec, (update_xr_kernel<S><<<blas_grid(a.len / vec_n<S>(), a.n), kThreads, 0, s>>>(
-                                a, x, r, p, Ap)));
+cudaError_t launch_cg_update_r(const BlasArgs& a, int prec, void* r, const void* Ap, cudaStream_t s) {
+    HISQ_PREC_SWITCH(prec, (update_r_kernel<S><<<blas_grid(a.len / vec_n<S>(), a.n), kThreads, 0, s>>>(
+                                a, r, Ap)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update_p(const BlasArgs& a, int prec, const void* r, void* p, cudaStream_t s) {
-    HISQ_PREC_SWITCH(prec, (update_p_kernel<S><<<blas_grid(a.len / vec_n<S>(), a.n), kThreads, 0, s>>>(
-                                a, r, p)));
+cudaError_t launch_cg_update_px(const BlasArgs& a, int prec, void* x, const void* r, void* p,
+                                cudaStream_t s) {
+    HISQ_PREC_SWITCH(prec, (update_px_kernel<S><<<blas_grid(a.len / vec_n<S>(), a.n), kThreads, 0, s>>>(
+                                a, x, r, p)));
     return cudaGetLastError();
 }
 

@@ -71,35 +71,41 @@ __device__ __forceinline__ void third_row(Link<RC>& m, const RC f) {
     m.e[8] = cmul(f, c2);
 }
 
-// Load one link of `recon` reals stored at [comp][vh] from `base` (already
-// offset to the (parity, mu) slab), site index `idx`. `sign` is the staggered
-// sign used by R12 (ignored otherwise).
+// Load one link of `recon` reals from `base` (the (parity, mu) block, laid
+// out as link_offset describes), site index `idx`, with streaming
+// (evict-first) loads: every link is read once per launch. `sign` is the
+// staggered sign used by R12 (ignored otherwise); sc holds the component
+// scales of 16-bit links.
 template <typename LC, int RECON, typename RC>
 __device__ __forceinline__ void load_link(Link<RC>& m, const LC* __restrict__ base, int vh,
                                           int idx, typename Traits<float>::R inv_s_f,
                                           double inv_s_d, int sign, const float* sc) {
     using R = decltype(RC{}.x);
     constexpr int NC = (RECON == 18) ? 9 : (RECON == 14 ? 7 : 6);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        const auto v = link_elem(__ldcs(base + (size_t)c * vh + idx), sc[c]);
+    auto put = [&](int c, LC raw) {
+        const auto v = link_elem(raw, sc[c]);
         m.e[c].x = (R)v.x;
         m.e[c].y = (R)v.y;
-    }
-    if (RECON == 18) {
+    };
+    // stored components, converted as they arrive (no raw copy of the link)
+    if constexpr (LinkPair<LC>::paired) {
+        using V = typename LinkPair<LC>::V;
+        const V* pb = reinterpret_cast<const V*>(base);
 #pragma unroll
-        for (int c = 6; c < 9; ++c) {
-            const auto v = link_elem(__ldcs(base + (size_t)c * vh + idx), sc[c]);
-            m.e[c].x = (R)v.x;
-            m.e[c].y = (R)v.y;
+        for (int p = 0; p < NC / 2; ++p) {
+            LC a, b;
+            split_pair(__ldcs(pb + (size_t)p * vh + idx), a, b);
+            put(2 * p, a);
+            put(2 * p + 1, b);
         }
-    } else if (RECON == 14) {
-        const auto zv = link_elem(__ldcs(base + (size_t)(NC - 1) * vh + idx), sc[NC - 1]);
-        RC z;
-        z.x = (R)zv.x;
-        z.y = (R)zv.y;
-        third_row(m, z);
+        if constexpr (NC & 1) put(NC - 1, __ldcs(base + (size_t)(NC - 1) * vh + idx));
     } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) put(c, __ldcs(base + (size_t)c * vh + idx));
+    }
+    if constexpr (RECON == 14) {
+        third_row(m, m.e[6]);
+    } else if constexpr (RECON == 12) {
         RC f;
         const R inv_s = (sizeof(R) == 8) ? (R)inv_s_d : (R)inv_s_f;
         f.x = sign > 0 ? inv_s : -inv_s;
@@ -213,21 +219,33 @@ __device__ __forceinline__ void mv_packed(f2x (&acc)[3], const PLink& pl, const 
         }
 }
 
-// Asynchronous bulk prefetch of [elem0, elem1) of one link component slab
-// into L2 (no registers, no completion to wait for). The range is clamped to
-// the slab and widened to 16-byte boundaries.
+// Asynchronous bulk prefetch of elements [elem0, elem1) of a run of `len`
+// link elements into L2 (no registers, no completion to wait for). The range
+// is clamped to the run and widened to 16-byte boundaries.
 template <typename LC>
-__device__ __forceinline__ void prefetch_slab(const LC* slab, int vh, long long elem0, long long elem1) {
+__device__ __forceinline__ void prefetch_slab(const LC* slab, long long len, long long elem0, long long elem1) {
     if (elem0 < 0) elem0 = 0;
-    if (elem1 > vh) elem1 = vh;
+    if (elem1 > len) elem1 = len;
     if (elem1 <= elem0) return;
     uintptr_t b0 = reinterpret_cast<uintptr_t>(slab + elem0) & ~(uintptr_t)15;
     uintptr_t b1 = (reinterpret_cast<uintptr_t>(slab + elem1) + 15) & ~(uintptr_t)15;
-    const uintptr_t lim = reinterpret_cast<uintptr_t>(slab + vh) & ~(uintptr_t)15;
+    const uintptr_t lim = reinterpret_cast<uintptr_t>(slab + len) & ~(uintptr_t)15;
     if (b1 > lim) b1 = lim;
     if (b1 <= b0) return;
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"((unsigned)(b1 - b0))
                  : "memory");
+}
+
+// Site range [e0, e1) of every stored component of one (parity, mu) block.
+template <typename LC>
+__device__ __forceinline__ void prefetch_block(const LC* block, int nc, int vh, long long e0, long long e1) {
+    if constexpr (LinkPair<LC>::paired) {
+        const int np = nc & ~1;
+        for (int p = 0; p < np / 2; ++p) prefetch_slab(block + (size_t)2 * p * vh, 2ll * vh, 2 * e0, 2 * e1);
+        if (nc & 1) prefetch_slab(block + (size_t)np * vh, (long long)vh, e0, e1);
+    } else {
+        for (int c = 0; c < nc; ++c) prefetch_slab(block + (size_t)c * vh, (long long)vh, e0, e1);
+    }
 }
 
 // Lanes of the first warp prefetch into L2 the links that the block's sites
@@ -239,18 +257,15 @@ __device__ __forceinline__ void prefetch_tile_links(const LC* Ub, const LC* Nb, 
     if (threadIdx.y != 0 || threadIdx.x >= 32) return;
     const int q = 1 - p;
     const int vh = g.vh;
-    constexpr int per_dir = 2 * (NCU + NCN);
-    for (int job = threadIdx.x; job < 4 * per_dir; job += 32) {
-        const int mu = job / per_dir;
-        int r = job - mu * per_dir;
-        const bool naik = r >= 2 * NCU;
-        if (naik) r -= 2 * NCU;
+    // 16 jobs: direction mu, field (fat, Naik), forward or backward
+    for (int job = threadIdx.x; job < 16; job += 32) {
+        const int mu = job >> 2;
+        const bool naik = (job >> 1) & 1;
+        const bool back = job & 1;
         const int nc = naik ? NCN : NCU;
-        const bool back = r >= nc;
-        const int c = back ? r - nc : r;
         const LC* base = naik ? Nb : Ub;
         const int par = back ? q : p;
-        const LC* slab = base + ((size_t)(par * 4 + mu) * nc + c) * vh;
+        const LC* block = base + (size_t)(par * 4 + mu) * nc * vh;
         long long e0 = hb, e1 = (long long)hb + nb;
         if (back) {
             const int d = naik ? 3 : 1;
@@ -263,7 +278,7 @@ __device__ __forceinline__ void prefetch_tile_links(const LC* Ub, const LC* Nb, 
                 e1 -= (long long)d * s;
             }
         }
-        prefetch_slab(slab, vh, e0, e1);
+        prefetch_block(block, nc, vh, e0, e1);
     }
 }
 

@@ -88,8 +88,7 @@ struct DslashPipe {
         const int hn = neighbour<E>();
         const LC* base = (NAIK ? Nb : Ub) + (size_t)((BACK ? q : p) * 4 + MU) * NC * vh;
         const int li = BACK ? hn : h;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) b.l[c] = __ldcs(base + (size_t)c * vh + li);
+        load_link_raw<LC, NC>(b.l, base, vh, li);
 #pragma unroll
         for (int j = 0; j < RPT; ++j) {
             const SC* s = reinterpret_cast<const SC*>(a.in[k0 + j]);
@@ -108,10 +107,10 @@ struct DslashPipe {
         Link<RC> m;
 #pragma unroll
         for (int c = 0; c < 6; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
-        if (REC == 18) {
+        if constexpr (REC == 18) {
 #pragma unroll
             for (int c = 6; c < 9; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
-        } else if (REC == 14) {
+        } else if constexpr (REC == 14) {
             third_row(m, link_elem(b.l[NC - 1], sc[NC - 1]));
         } else {
             // staggered sign of this site's mu links; eta_mu(x - mu) = eta_mu(x),

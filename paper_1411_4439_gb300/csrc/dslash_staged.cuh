@@ -77,7 +77,8 @@ __device__ __forceinline__ int staged_offset(int lt) {
     return lt == 0 ? 0 : lt == 1 ? NCU : lt == 2 ? 2 * NCU : 2 * NCU + NCN;
 }
 
-// Link of `recon` reals from a shared stage run: component c at base[c * ts + idx].
+// Link of `recon` reals from a shared stage region laid out as a global block
+// with V_h = ts: component c of tile site idx at base[link_offset(c, nc, ts, idx)].
 template <typename LC, int RECON, typename RC>
 __device__ __forceinline__ void load_link_shared(Link<RC>& m, const LC* base, int ts, int idx, float inv_s_f,
                                                  double inv_s_d, int sign, const float* sc) {
@@ -85,12 +86,12 @@ __device__ __forceinline__ void load_link_shared(Link<RC>& m, const LC* base, in
     constexpr int NC = (RECON == 18) ? 9 : (RECON == 14 ? 7 : 6);
 #pragma unroll
     for (int c = 0; c < (RECON == 18 ? 9 : 6); ++c) {
-        const auto v = link_elem(base[c * ts + idx], sc[c]);
+        const auto v = link_elem(base[link_offset<LC>(c, NC, ts, idx)], sc[c]);
         m.e[c].x = (R)v.x;
         m.e[c].y = (R)v.y;
     }
     if (RECON == 14) {
-        const auto zv = link_elem(base[(NC - 1) * ts + idx], sc[NC - 1]);
+        const auto zv = link_elem(base[link_offset<LC>(NC - 1, NC, ts, idx)], sc[NC - 1]);
         RC zz;
         zz.x = (R)zv.x;
         zz.y = (R)zv.y;
@@ -162,12 +163,20 @@ __device__ __forceinline__ unsigned issue_direction(LC* buf, const LC* Ub, const
         const int nc = NC_of<NCU, NCN>(lt);
         const LC* base = (lt >= 2) ? Nb : Ub;
         const int par = back ? q : p;
-        const int off = staged_offset<NCU, NCN>(lt);
-        for (int c = 0; c < nc; ++c) {
-            const LC* slab = base + ((size_t)(par * 4 + mu) * nc + c) * vh;
+        // the stage region of this link type mirrors the global block layout
+        // (link_offset) with V_h replaced by the tile size
+        LC* region = buf + (size_t)staged_offset<NCU, NCN>(lt) * TS;
+        const LC* block = base + (size_t)(par * 4 + mu) * nc * vh;
+        const int words = LinkPair<LC>::paired ? (nc + 1) / 2 : nc;
+        for (int w = 0; w < words; ++w) {
+            // a word is a component pair, or a single component (FP64, odd last)
+            const bool pair = LinkPair<LC>::paired && 2 * w + 1 < nc;
+            const int c0 = LinkPair<LC>::paired ? 2 * w : w;
+            const int per = pair ? 2 : 1;
             for (int k = 0; k < nrun[lt]; ++k)
-                bulk_copy_g2s(buf + (size_t)(off + c) * TS + dst[lt][k], slab + src[lt][k],
-                              (unsigned)cnt[lt][k] * sizeof(LC), bar);
+                bulk_copy_g2s(region + link_offset<LC>(c0, nc, TS, dst[lt][k]),
+                              block + link_offset<LC>(c0, nc, vh, src[lt][k]),
+                              (unsigned)cnt[lt][k] * per * sizeof(LC), bar);
         }
     }
     return bytes;

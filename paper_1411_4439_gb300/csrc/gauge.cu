@@ -1,10 +1,12 @@
 // Link packing and reconstruction (Sec. 1: links stored in fewer reals).
 //
 // Canonical input: complex128 [4][V][3][3], lexicographic site order.
-// Internal output: [parity][mu][complex component][V_h] in the storage
-// precision (FP64, FP32, or 16-bit fixed point with one scale per stored
-// component), so that the Dslash reads each component of 32 consecutive
-// sites with one coalesced warp access.
+// Internal output: per (parity, mu) block the stored components of V_h
+// sites in the storage precision (FP64, FP32, or 16-bit fixed point with one
+// scale per stored component): FP64 as [component][V_h]; FP32 and 16-bit as
+// [component pair][V_h] (two components of a site in one 16- or 8-byte word)
+// and the odd last component as [V_h] (link_offset). A warp's 32 consecutive
+// sites read each word with one coalesced access.
 //   R18: 9 components; R14: rows 1-2 and z with row3 = z conj(row1 x row2);
 //   R12: rows 1-2 with row3 = (sigma/s) conj(row1 x row2).
 // Every packed link is reconstructed here in FP64 and compared with the
@@ -150,8 +152,8 @@ __global__ void pack_kernel(Geom g, const double2* __restrict__ canon, int recon
         for (int c = 0; c < 9; ++c) m[c] = canon[w * 9 + c];
         const int sg = (recon == 12) ? staggered_sign(g, s, mu, hop) : 1;
         worst = fmax(worst, encode(m, recon, sg, inv_s, enc));
-        C* dst = out + ((size_t)(s.parity * 4 + mu) * nc) * g.vh + s.h;
-        for (int c = 0; c < nc; ++c) dst[(size_t)c * g.vh] = store_comp<C>(enc[c], comp_scale, c);
+        C* block = out + ((size_t)(s.parity * 4 + mu) * nc) * g.vh;
+        for (int c = 0; c < nc; ++c) block[link_offset<C>(c, nc, g.vh, s.h)] = store_comp<C>(enc[c], comp_scale, c);
     }
     if (err_bits != nullptr) atomic_max_nonneg(err_bits, worst);
 }

@@ -1105,8 +1105,8 @@ struct Solver {
     // One CG iteration on every active rhs.
     cudaError_t iterate(cudaStream_t s) const {
         cudaError_t e = apply_lo(s);
-        if (e == cudaSuccess) e = launch_cg_update_xr(blas(), prec, w->x_lo, w->r_lo, w->p_lo, w->Ap_lo, s);
-        if (e == cudaSuccess) e = launch_cg_update_p(blas(), prec, w->r_lo, w->p_lo, s);
+        if (e == cudaSuccess) e = launch_cg_update_r(blas(), prec, w->r_lo, w->Ap_lo, s);
+        if (e == cudaSuccess) e = launch_cg_update_px(blas(), prec, w->x_lo, w->r_lo, w->p_lo, s);
         return e;
     }
 
@@ -1185,7 +1185,7 @@ struct Solver {
             for (int i = 0; i < chunk; ++i) HISQ_CUDA(iterate(s));
             return HISQ_OK;
         }
-        GraphKey key{chunk, mass, mu, tune.rpt * 100 + tune.minb * 10 + tune.layout};
+        GraphKey key{chunk, mass, mu, tune.kind * 1000 + tune.rpt * 100 + tune.minb * 10 + tune.layout};
         auto it = w->graphs.find(key);
         if (it == w->graphs.end()) {
             if (w->graphs.size() >= 8) {

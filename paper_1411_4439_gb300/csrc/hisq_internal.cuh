@@ -76,16 +76,57 @@ __device__ __forceinline__ float2 link_elem(short2 v, float sc) {
     return make_float2((float)v.x * sc, (float)v.y * sc);
 }
 
+// Link slab layout of one (parity, mu) block of nc stored components. FP32
+// and 16-bit storage keep components (2p, 2p+1) of a site side by side, so a
+// thread reads two of them with one 16- or 8-byte load: [nc/2 pairs][V_h]
+// then [V_h] of the last component when nc is odd. FP64 keeps [nc][V_h]
+// (one double2 is already 16 bytes).
+template <typename LC> struct LinkPair { static constexpr bool paired = false; };
+template <> struct LinkPair<float2> {
+    static constexpr bool paired = true;
+    using V = float4;
+};
+template <> struct LinkPair<short2> {
+    static constexpr bool paired = true;
+    using V = short4;
+};
+
+__device__ __forceinline__ void split_pair(const float4& w, float2& a, float2& b) {
+    a = make_float2(w.x, w.y);
+    b = make_float2(w.z, w.w);
+}
+__device__ __forceinline__ void split_pair(const short4& w, short2& a, short2& b) {
+    a = make_short2(w.x, w.y);
+    b = make_short2(w.z, w.w);
+}
+
+// Offset (in stored complex numbers) of component c of site idx in a block.
+template <typename LC>
+__host__ __device__ __forceinline__ size_t link_offset(int c, int nc, long long vh, long long idx) {
+    if (!LinkPair<LC>::paired) return (size_t)c * vh + idx;
+    const int np = nc & ~1;
+    return c < np ? ((size_t)(c >> 1) * vh + idx) * 2 + (c & 1) : (size_t)np * vh + idx;
+}
+
+// Components [0, NC) of the link of site idx from a block, streaming loads.
+template <typename LC, int NC, int NL>
+__device__ __forceinline__ void load_link_raw(LC (&l)[NL], const LC* __restrict__ block, int vh, int idx) {
+    static_assert(NC <= NL, "link buffer too small");
+    if constexpr (LinkPair<LC>::paired) {
+        using V = typename LinkPair<LC>::V;
+        const V* pb = reinterpret_cast<const V*>(block);
+#pragma unroll
+        for (int p = 0; p < NC / 2; ++p) split_pair(__ldcs(pb + (size_t)p * vh + idx), l[2 * p], l[2 * p + 1]);
+        if constexpr (NC & 1) l[NC - 1] = __ldcs(block + (size_t)(NC - 1) * vh + idx);
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) l[c] = __ldcs(block + (size_t)c * vh + idx);
+    }
+}
+
 __device__ __forceinline__ double2 ld_c(const double2* p) { return __ldg(p); }
 __device__ __forceinline__ float2 ld_c(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ float2 ld_c(const __half2* p) { return __half22float2(__ldg(p)); }
-
-// Streaming loads for data read once per launch (links): evict-first hint.
-__device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
-__device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
-__device__ __forceinline__ float2 ld_stream(const __half2* p) {
-    return __half22float2(__ldcs(p));
-}
 
 // The value a store of v through p leaves in memory, in arithmetic precision.
 __device__ __forceinline__ double2 stored_value(double2 v, const double2*) { return v; }
@@ -94,9 +135,6 @@ __device__ __forceinline__ float2 stored_value(float2 v, const __half2*) {
     return __half22float2(__float22half2_rn(v));
 }
 
-__device__ __forceinline__ double2 to_float2_or_double2(double2 v) { return v; }
-__device__ __forceinline__ float2 to_float2_or_double2(float2 v) { return v; }
-__device__ __forceinline__ float2 to_float2_or_double2(__half2 v) { return __half22float2(v); }
 
 __device__ __forceinline__ void st_c(double2* p, double2 v) { *p = v; }
 __device__ __forceinline__ void st_c(float2* p, float2 v) { *p = v; }
@@ -250,12 +288,11 @@ struct BlasArgs {
     double freeze2;      // norm_bb stores it into cg->freeze2
     double alpha_max;    // norm_bb stores it into cg->alpha_max
 };
-// x_lo += alpha p; r -= alpha Ap; rr' = |r|^2 -> beta = rr'/rr, rr = rr'
-cudaError_t launch_cg_update_xr(const BlasArgs& a, int prec, void* x, void* r,
-                                const void* p, const void* Ap, cudaStream_t s);
-// p = r + beta p
-cudaError_t launch_cg_update_p(const BlasArgs& a, int prec, const void* r, void* p,
-                               cudaStream_t s);
+// r -= alpha Ap; rr' = |r|^2 -> beta = rr'/rr, rr = rr'
+cudaError_t launch_cg_update_r(const BlasArgs& a, int prec, void* r, const void* Ap, cudaStream_t s);
+// x_lo += alpha p; p = r + beta p (one pass over the old p)
+cudaError_t launch_cg_update_px(const BlasArgs& a, int prec, void* x, const void* r, void* p,
+                                cudaStream_t s);
 // x_hi (FP64) += x_lo / scale ; x_lo = 0
 cudaError_t launch_accum_solution(const BlasArgs& a, int prec, double2* x_hi, void* x_lo,
                                   cudaStream_t s);

@@ -65,3 +65,32 @@ def test_two_rank_max_reduction_over_gloo():
         assert p.exitcode == 0
     got = dict(q.get(timeout=10) for _ in range(2))
     assert got == {0: 2.0, 1: 2.0}
+
+
+def test_reference_arm_is_silent_on_other_ranks(monkeypatch, capsys):
+    """Under torchrun only rank 0 runs and prints the reference line."""
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert capsys.readouterr().out == ""
+
+
+def test_roofline_traffic_only_for_the_captured_mapping():
+    name, traffic = bench.dslash_kernel_name(4, 2, 16, (32, 32, 32, 8))
+    assert "dslash_pipe_kernel" in name and "depth=2" in name and traffic > 0
+    assert bench.dslash_kernel_name(8, 2, 0, (32, 32, 32, 8))[1] is None
+    assert bench.dslash_kernel_name(4, 2, 16, (48, 48, 48, 12))[1] is None
+
+
+def test_warmup_is_clamped_to_three():
+    seen = {}
+
+    def fake(args):
+        seen["warmup"] = args.warmup
+    old = bench.run_reference
+    bench.run_reference = fake
+    try:
+        bench.main(["--impl", "reference", "--warmup", "1"])
+    finally:
+        bench.run_reference = old
+    assert seen["warmup"] == 3
