@@ -6,7 +6,7 @@
 // For every direction the tile needs four link runs per component: forward U
 // and N of its own sites, and backward U and N of its neighbours. With the
 // tile made of whole rows inside one plane, every run is one contiguous slice
-// of the [parity][mu][component][V_h] link arrays (the backward y runs split
+// of a (parity, mu) link block, per component or component pair (the backward y runs split
 // in two where y wraps). One thread issues the copies of direction mu+1 into
 // the second buffer while all threads compute direction mu from the first,
 // so link loads neither wait in registers nor occupy them. The neighbour

@@ -274,7 +274,8 @@ def hisq_gauge_info(g: Gauge) -> dict:
 def hisq_set_dslash_mapping(g: Gauge, rhs_per_thread: int, min_blocks: int = 0,
                             flags: int = 0) -> None:
     """Dslash rhs per thread, register budget (min blocks per SM) and HISQ_MAP_* flags
-    (packed f32x2 arithmetic, L2 link prefetch); 0 = automatic."""
+    (packed f32x2 arithmetic, L2 link prefetch, staged links, pipelined hops);
+    0 = automatic."""
     _check(library().hisq_set_dslash_mapping(g.handle, int(rhs_per_thread), int(min_blocks),
                                              int(flags)))
 
