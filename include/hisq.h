@@ -62,7 +62,7 @@ enum {
     HISQ_EBREAKDOWN = 4,  /* CG breakdown: <p,Ap> <= 0 or not finite */
     HISQ_ENAN = 5,        /* non-finite value in a source or residual */
     HISQ_ECUDA = 6,       /* a CUDA runtime call failed; see hisq_last_error() */
-    HISQ_ETIMEOUT = 7,    /* reserved for bounded device-side waits */
+    HISQ_ETIMEOUT = 7,    /* a bounded device-side wait gave up (staged-link kernel) */
     HISQ_ENOMEM = 8       /* device allocation failed */
 };
 

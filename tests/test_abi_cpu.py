@@ -80,3 +80,13 @@ def test_null_handle_rejected(lib):
     f = lib.hisq_dslash
     f.restype = ctypes.c_int
     assert f(None, None, None, 1, 0, 1, None) == 1   # HISQ_EINVAL
+
+
+def test_binding_constants_match_the_header():
+    """Every HISQ_* enumerator of the header has the same value in the binding."""
+    import paper_1411_4439_gb300.hisq as B
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    pairs = re.findall(r"\b(HISQ_[A-Z0-9_]+)\s*=\s*(\d+)", text)
+    assert len(pairs) >= 25
+    for name, value in pairs:
+        assert getattr(B, name) == int(value), name
