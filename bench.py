@@ -448,7 +448,7 @@ def run_oracle_timing(args):
         O.dslash_parity(U, N, v, Ls, 0)
         return time.perf_counter() - t0
 
-    # configs[0]: 8^4, FP64, one rhs, m = 0.05, to convergence
+    # 8^4, FP64, one rhs, m = 0.05, to convergence
     L0 = (8, 8, 8, 8)
     U, N = gen.hisq_links(L0, seed=0)
     b = gen.z2_source(L0, 1, seed=0)
@@ -458,7 +458,7 @@ def run_oracle_timing(args):
           "cg_iterations": int(it[0]), "dslash_s_per_call_1rhs": dslash_s(U, N, b, L0),
           "sample": "complete solve"})
 
-    # configs[1]: 32^3x8, m = 0.01
+    # 32^3x8, m = 0.01
     U, N = gen.hisq_links(L, seed=LINK_SEED)
     b = gen.z2_source(L, NRHS, seed=SOURCE_SEED)
     iters_total, how = fp64_iterations(None)
@@ -480,7 +480,7 @@ def run_oracle_timing(args):
           "sample": f"2 CG iterations of each of the {NRHS} rhs in {procs} spawned processes"})
     del U, N, b
 
-    # configs[2]: 48^3x12, m = 0.0025, Gaussian; iteration count of the GPU FP64 solve
+    # 48^3x12, m = 0.0025, Gaussian; iteration count of the GPU FP64 solve
     L2 = (48, 48, 48, 12)
     U, N = gen.hisq_links(L2, seed=LINK_SEED)
     b = gen.gaussian_source(L2, 1, seed=SOURCE_SEED)
@@ -491,7 +491,7 @@ def run_oracle_timing(args):
           "sample": f"1 CG iteration of one rhs ({t_it:.2f} s/iteration)"})
     del U, N, b
 
-    # configs[3]: 16^4, mu = 0.1, full lattice M^dag M, m = 0.05
+    # 16^4, mu = 0.1, full lattice M^dag M, m = 0.05
     L3 = (16, 16, 16, 16)
     U, N = gen.hisq_links(L3, seed=LINK_SEED)
     v = O.to_full(gen.z2_source(L3, 1, seed=SOURCE_SEED), L3, 0) + \

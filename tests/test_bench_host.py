@@ -19,7 +19,7 @@ def test_algorithmic_bytes_match_oracle_model(n, fu, fn, sl, ss):
     assert bench.dslash_bytes_per_site(n, fu, fn, sl, ss) == O.dslash_bytes_algorithmic(n, fu, fn, sl, ss)
 
 
-def test_survey_byte_table_values():
+def test_byte_table_values():
     # bytes per output site: FP32 18/14 at n = 8 is 1408, FP16 12/14 at n = 1 is 440
     assert bench.dslash_bytes_per_site(8, 18, 14, 4, 4) == 1408
     assert bench.dslash_bytes_per_site(1, 12, 14, 2, 2) == 440
