@@ -534,7 +534,7 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-# further workloads (not the default headline line): --workload <name>
+# further workloads (besides the headline JSON line): --workload <name>
 # ---------------------------------------------------------------------------
 
 def _time_solve(H, torch, g, mass, mu, bt, xt, tol, params, stream, reps=1):
