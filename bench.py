@@ -275,9 +275,10 @@ def run_gpu(args):
         e1.synchronize()
         durs.append(e0.elapsed_time(e1) / 1e3)
         # per iteration: two Dslash, update_r, update_px; per reliable update:
-        # accumulate, two FP64 Dslash, rescale; per solve: transpose b into the
-        # SoA workspace, norm |b|, copy the residual, rescale, transpose x out
-        launches += 4 * st.total_iters + 4 * st.reliable_updates + 5
+        # accumulate, two FP64 Dslash, rescale; per solve: norm |b|, copy the
+        # residual, rescale (and with SoA workspaces a transpose of b in and x out)
+        launches += 4 * st.total_iters + 4 * st.reliable_updates + 3
+        launches += 2 if params.spinor_layout == H.HISQ_SOA else 0
         stats_last = st
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0

@@ -326,7 +326,7 @@ typedef struct {
     int check_every;       /* host convergence poll interval (10) */
     int use_graphs;        /* 1: replay iterations from a captured CUDA graph (1) */
     int rhs_per_thread;    /* Dslash rhs per thread: 0 = auto, else 1/2/4/8 */
-    hisq_layout spinor_layout; /* layout of the CG's internal vectors (HISQ_SOA) */
+    hisq_layout spinor_layout; /* layout of the CG's internal vectors (HISQ_AOS) */
 } hisq_cg_params;
 
 typedef struct {

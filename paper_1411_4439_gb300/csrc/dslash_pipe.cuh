@@ -162,6 +162,43 @@ struct DslashPipe {
     }
 };
 
+// Epilogue with x read before the hops (xr, storage precision): the load is
+// long done when the hops finish, where reading x after them measured 8 % of
+// the launch at 32^3x8, n = 8. out = cx x + cd (D in), optional Re<x, out>.
+template <typename SC, int RPT, int EPI, int LAYOUT, typename R, typename RC>
+__device__ __forceinline__ void epilogue_site_px(const DslashArgs& a, int h, int k0, const RC (&acc)[RPT][3],
+                                                 const SC (&xr)[RPT][3], R (&red0)[RPT], R (&red1)[RPT]) {
+    static_assert(EPI == EPI_X, "the pipelined kernel's early-x epilogue serves EPI_X only");
+    const int vh = a.g.vh;
+    const R cx = (R)a.cx, cd = (R)a.cd;
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        RC w[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const RC xv = to_rc(xr[j][c]);
+            w[c].x = fma(cd, acc[j][c].x, cx * xv.x);
+            w[c].y = fma(cd, acc[j][c].y, cx * xv.y);
+            if (a.red_mode == RED_DOT_XW) {
+                red0[j] = fma(xv.x, w[c].x, red0[j]);
+                red0[j] = fma(xv.y, w[c].y, red0[j]);
+            }
+        }
+        SC* o = reinterpret_cast<SC*>(a.out[k0 + j]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st_c(o + spinor_index<LAYOUT>(h, c, vh), w[c]);
+        if (a.red_mode == RED_NORM_MAX_W) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const RC sv = stored_value(w[c], (const SC*)o);
+                const R n2 = sv.x * sv.x + sv.y * sv.y;
+                red0[j] += n2;
+                red1[j] = fmax(red1[j], sqrt(n2));
+            }
+        }
+    }
+}
+
 template <typename S, typename LS, int RU, int RN, int RPT, int MINB, int DEPTH, int EPI, int LAYOUT>
 __global__ void __launch_bounds__(256, MINB) dslash_pipe_kernel(const DslashArgs a) {
     using R = typename Traits<S>::R;
@@ -187,9 +224,21 @@ __global__ void __launch_bounds__(256, MINB) dslash_pipe_kernel(const DslashArgs
                 acc[j][c].x = (R)0;
                 acc[j][c].y = (R)0;
             }
-        DslashPipe<S, LS, RU, RN, RPT, DEPTH, LAYOUT> pipe(a, h, k0, acc);
-        pipe.run();
-        epilogue_site<SC, RPT, EPI, LAYOUT>(a, h, k0, acc, red0, red1);
+        if constexpr (EPI == EPI_X) {
+            SC xr[RPT][3];
+#pragma unroll
+            for (int j = 0; j < RPT; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    xr[j][c] = __ldg(reinterpret_cast<const SC*>(a.x[k0 + j]) + spinor_index<LAYOUT>(h, c, vh));
+            DslashPipe<S, LS, RU, RN, RPT, DEPTH, LAYOUT> pipe(a, h, k0, acc);
+            pipe.run();
+            epilogue_site_px<SC, RPT, EPI, LAYOUT>(a, h, k0, acc, xr, red0, red1);
+        } else {
+            DslashPipe<S, LS, RU, RN, RPT, DEPTH, LAYOUT> pipe(a, h, k0, acc);
+            pipe.run();
+            epilogue_site<SC, RPT, EPI, LAYOUT>(a, h, k0, acc, red0, red1);
+        }
     }
     if (a.red_mode == RED_NONE) return;
     block_reduce_finish<RPT>(a, k0, red0, red1);

@@ -942,7 +942,7 @@ extern "C" void hisq_cg_default_params(hisq_cg_params* p) {
     p->check_every = 10;
     p->use_graphs = 1;
     p->rhs_per_thread = 0;
-    p->spinor_layout = HISQ_SOA;
+    p->spinor_layout = HISQ_AOS;   // the ABI layout: no transposes, and the early-x epilogue fits in registers
 }
 
 namespace {
