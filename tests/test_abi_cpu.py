@@ -90,3 +90,35 @@ def test_binding_constants_match_the_header():
     assert len(pairs) >= 25
     for name, value in pairs:
         assert getattr(B, name) == int(value), name
+
+
+def test_new_entry_points_reject_bad_arguments_before_cuda(lib):
+    """Tuned load, bundle tuner, autotuner, batched solve and mapping calls
+    validate their arguments before any CUDA call."""
+    import paper_1411_4439_gb300.hisq as B
+    L = (ctypes.c_int * 4)(4, 4, 4, 4)
+    h = ctypes.c_void_p()
+    f = lib.hisq_gauge_load_tuned
+    f.restype = ctypes.c_int
+    assert f(L, None, None, 0, B.HISQ_F32, 0, ctypes.c_double(1e-10), None, ctypes.byref(h)) == B.HISQ_EINVAL
+    assert f(L, None, None, 0, 7, 4, ctypes.c_double(1e-10), None, ctypes.byref(h)) == B.HISQ_EINVAL
+    assert f(L, None, None, 0, B.HISQ_F32, 4, ctypes.c_double(1e-10), None, None) == B.HISQ_EINVAL
+    f = lib.hisq_autotune_bundle
+    f.restype = ctypes.c_int
+    assert f(None, 8, B.HISQ_F32, B.HISQ_AOS, 5, None, None) == B.HISQ_EINVAL
+    f = lib.hisq_autotune_dslash
+    f.restype = ctypes.c_int
+    assert f(None, 8, B.HISQ_F32, B.HISQ_AOS, 5, None, None, None, None) == B.HISQ_EINVAL
+    f = lib.hisq_cg_solve_batched
+    f.restype = ctypes.c_int
+    assert f(None, 1, None, None, None) == B.HISQ_EINVAL
+    probs = (B.hisq_cg_problem * 1)()
+    assert f(probs, 0, None, None, None) == B.HISQ_EINVAL
+    assert f(probs, 65, None, None, None) == B.HISQ_EINVAL
+    assert f(probs, 1, None, None, None) == B.HISQ_EINVAL       # NULL handle in the problem
+    f = lib.hisq_set_dslash_mapping
+    f.restype = ctypes.c_int
+    assert f(None, 4, 2, B.HISQ_MAP_PIPELINED2) == B.HISQ_EINVAL
+    err = lib.hisq_last_error
+    err.restype = ctypes.c_char_p
+    assert b"NULL handle" in err()
