@@ -397,3 +397,132 @@ def test_trace_word_matches_dense_trace():
         got = O.trace_word_bilinear(U, N, eta, m, mu, orders)
         assert np.allclose(got, W[idx, idx], rtol=1e-9, atol=1e-11)
     assert abs(exact_1) > 0 and abs(exact_11) > 0 and abs(exact_2) > 0
+
+
+# ---------------------------------------------------------------------------
+# The residual checker that decides every CG parity test: pinned to a residual
+# fixed independently of it (a dense matrix product and numpy's own norm, and
+# the closed-form eigenvalue of the free field)
+# ---------------------------------------------------------------------------
+
+def test_true_relative_residual_equals_dense_residual_of_a_perturbed_solution():
+    L, m = (4, 4, 4, 4), 0.05
+    U, N = gen.hisq_links(L, seed=61)
+    vh = 128
+    A = O.dense_matrix(lambda q: O.apply_Ae(U, N, q, L, m), (vh, 3))
+    rng = np.random.default_rng(62)
+    n = 3
+    # rhs of very different norms, so that a norm taken over all rhs together
+    # or a missing division by |b| shows
+    b = gen.z2_source(L, n, 63) * np.array([1.0, 1e-3, 250.0])[:, None, None]
+    x_lu = np.linalg.solve(A, b.reshape(n, -1).T).T
+    delta = rng.standard_normal(x_lu.shape) + 1j * rng.standard_normal(x_lu.shape)
+    delta *= np.array([1e-6, 1e-9, 1e-2])[:, None]      # residuals of about 1e-5 .. 1e-9
+    x = (x_lu + delta).reshape(b.shape)
+    want = np.array([np.linalg.norm(A @ delta[k]) / np.linalg.norm(b[k].ravel()) for k in range(n)])
+    got = O.true_relative_residual(lambda q: O.apply_Ae(U, N, q, L, m), x, b)
+    assert got.shape == (n,)
+    # x_lu is exact to ~1e-15 relative, far below the planted residuals
+    np.testing.assert_allclose(got, want, rtol=1e-6)
+    # a squared norm (|r|^2/|b|^2) or |r|^2/|b| would be off by orders of magnitude
+    assert np.all(got > 1e-10) and np.all(got < 1e-3)
+
+
+@pytest.mark.parametrize("c", [0.0, 0.5, 1.5])
+def test_true_relative_residual_of_a_free_field_eigenvector(c):
+    # b an eigenvector of A_e with eigenvalue lam (closed form) and x = c b / lam:
+    # b - A x = (1 - c) b, so the relative residual is |1 - c| exactly
+    L, m = (8, 8, 8, 8), 0.05
+    c1, c3 = 9.0 / 8.0, -1.0 / 24.0
+    U, N = gen.free_field_links(L, c1, c3)
+    v, p = plane_wave(L, [1, 2, 0, 1], [1.0, 0.5j, -0.25])
+    lam = 4 * m * m + sum(s * s for s in free_s(p, c1, c3)).real
+    b = np.concatenate([O.to_half(v, L, 0), 3.0 * O.to_half(v, L, 0)])
+    x = np.concatenate([c * b[:1] / lam, np.zeros_like(b[1:])])
+    got = O.true_relative_residual(lambda q: O.apply_Ae(U, N, q, L, m), x, b)
+    np.testing.assert_allclose(got, [abs(1.0 - c), 1.0], rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# The reading of "FP16 link storage": 16-bit fixed point per stored component,
+# not IEEE half. A model of the mixed-precision solver (half spinors with a
+# per-rhs scale, FP32 solution increment, FP64 reliable update every 50
+# iterations or when the residual fell by 10x) on the light-mass system
+# m = 0.0025 converges with fixed-point links and fails with IEEE-half links.
+# ---------------------------------------------------------------------------
+
+def _links_ieee_half(a):
+    return a.real.astype(np.float16).astype(np.float64) + 1j * a.imag.astype(np.float16).astype(np.float64)
+
+
+def _links_fixed16(a):
+    # one scale per stored complex component (i, j) of the field: the largest
+    # |Re| or |Im| of that component over the field maps to 32767
+    out = np.empty_like(a)
+    for i in range(3):
+        for j in range(3):
+            c = a[..., i, j]
+            s = max(np.abs(c.real).max(), np.abs(c.imag).max()) / 32767.0
+            out[..., i, j] = (np.rint(c.real / s) + 1j * np.rint(c.imag / s)) * s
+    return out
+
+
+def _half_store(v, scale):
+    w = v * scale
+    return (w.real.astype(np.float16).astype(np.float64) + 1j * w.imag.astype(np.float16).astype(np.float64)) / scale
+
+
+def _mixed_cg_model(Doe, Deo, A, b, m, tol=1e-10, maxiter=12000, every=50, delta=0.1):
+    """(iterations, final true relative residual) of the storage model."""
+    m2 = 4 * m * m
+    x = np.zeros_like(b)
+    bb = np.vdot(b, b).real
+    s = 1.0 / np.abs(b).max()
+    r = _half_store(b, s)
+    p = r.copy()
+    xl = np.zeros_like(b)
+    rr = np.vdot(r, r).real
+    rr_rel, since, res = rr, 0, 1.0
+    for it in range(1, maxiter + 1):
+        t = _half_store(Doe @ p, s)
+        Ap = _half_store(m2 * p - Deo @ t, s)
+        alpha = rr / np.vdot(p, Ap).real
+        r = _half_store(r - alpha * Ap, s)
+        xl = (xl + alpha * p).astype(np.complex64).astype(np.complex128)
+        rr_new = np.vdot(r, r).real
+        beta, rr = rr_new / rr, rr_new
+        p = _half_store(r + beta * p, s)
+        since += 1
+        if since >= every or rr <= delta * delta * rr_rel:
+            x, xl = x + xl, np.zeros_like(xl)
+            rt = b - A @ x                      # FP64 true residual
+            res = np.sqrt(np.vdot(rt, rt).real / bb)
+            if res <= tol or not np.isfinite(res) or res > 1e2:
+                return it, res
+            s = 1.0 / np.abs(rt).max()
+            r, p = _half_store(rt, s), _half_store(p, s)
+            rr = rr_rel = np.vdot(r, r).real
+            since = 0
+    return maxiter, res
+
+
+@pytest.mark.parametrize("seed", [1, 4])
+def test_sixteen_bit_fixed_point_links_converge_where_ieee_half_links_fail(seed):
+    L, m = (4, 4, 4, 4), 0.0025
+    U, N = gen.hisq_links(L, seed=seed)
+    vh = 128
+
+    def blocks(Uq, Nq):
+        Doe = O.dense_matrix(lambda q: O.dslash_parity(Uq, Nq, q, L, 1), (vh, 3))
+        Deo = O.dense_matrix(lambda q: O.dslash_parity(Uq, Nq, q, L, 0), (vh, 3))
+        return Doe, Deo
+
+    Doe, Deo = blocks(U, N)
+    A = 4 * m * m * np.eye(3 * vh) - Deo @ Doe
+    b = gen.gaussian_source(L, 1, seed + 100)[0].ravel()
+    it_ref, res_ref = _mixed_cg_model(Doe, Deo, A, b, m)
+    assert res_ref <= 1e-10
+    it_fx, res_fx = _mixed_cg_model(*blocks(_links_fixed16(U), _links_fixed16(N)), A, b, m)
+    assert res_fx <= 1e-10 and it_fx <= 1.3 * it_ref
+    _, res_half = _mixed_cg_model(*blocks(_links_ieee_half(U), _links_ieee_half(N)), A, b, m)
+    assert not res_half <= 1e-10
