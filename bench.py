@@ -1,23 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the multi-rhs HISQ CG hot path on one GB300 (or N, weak scaling).
 
-Workload (the multi-rhs FP32 configuration): 32^3 x 8 lattice, synthetic
-Haar-random fat links (0.9 x SU(3), r18) and Naik links (-1/24 x U(3), r14)
-with staggered phases and an antiperiodic t boundary folded in, a bundle of
-n = 8 complex Z2 sources, m = 0.01, mu = 0, even-odd system
-(4m^2 - D_eo D_oe) x_e = b_e solved to a true relative residual of 1e-10
-with FP32 inner iterations and FP64 reliable updates every 50 iterations.
+Workload (the mixed-precision multi-rhs configuration): 48^3 x 12 lattice,
+synthetic Haar-random fat links (0.9 x SU(3), stored in 18 reals) and Naik
+links (-1/24 x U(3), 14 reals) with staggered phases and an antiperiodic t
+boundary folded in, all link reals stored as 16-bit fixed point, a bundle of
+n = 8 Gaussian complex sources, m = 0.0025, mu = 0, even-odd system
+(4m^2 - D_eo D_oe) x_e = b_e solved to a true relative residual of 1e-10 with
+FP16 spinor storage and FP32 arithmetic in the inner iteration, FP64
+reliable updates (true residual with FP64 links) and an FP64 solution.
 
 One step = one complete hisq_cg_solve of the bundle with the gauge field
 loaded and the sources resident in HBM. value = seconds per right-hand side
 (whole job: wall time of the slowest rank / rhs solved by all ranks).
 
 Also reported on the same JSON line:
-  roofline      the multi-rhs Dslash (the dominant kernel): algorithmic bytes
-                per launch / CUDA-event launch time vs the measured HBM peak
-  dslash        the same Dslash as GB/s, GFlop/s (1146 flop/site/rhs) and
-                fraction of 8 TB/s, plus an n sweep
-  fp64          the plain FP64 single-rhs GPU CG on the same system, s/rhs
+  roofline      the FP16 multi-rhs Dslash of the solve (the dominant kernel):
+                algorithmic flops (bytes) per launch / CUDA-event launch time
+                against the FP32 ALU peak (the measured HBM peak), L2 flushed
+                between launches
+  dslash        the same Dslash, and the FP32-storage one, as GB/s, GFlop/s
+                (1146 flop/site/rhs) and fractions of both peaks
+  fp64          the plain FP64 single-rhs GPU CG on the same system and
+                source 0 (the comparison of "mixed vs FP64"), s/rhs
+  configs1      the multi-rhs FP32 configuration (32^3x8, n = 8, m = 0.01)
   e2e           the same solve through the C ABI with pinned host buffers
   cpu_baseline  the FP64 numpy oracle on the host cores (bounded sample)
 
@@ -42,29 +48,38 @@ if ROOT not in sys.path:
 
 METRIC = "multi-RHS Dslash HBM GB/s (frac of 8 TB/s); CG s/rhs to 1e-10, mixed vs FP64"
 UNIT = "s/rhs"
-L = (32, 32, 32, 8)
+# the headline workload: mixed precision, 48^3x12
+L = (48, 48, 48, 12)
 NRHS = 8
-MASS = 0.01
+MASS = 0.0025
 TOL = 1e-10
-RELIABLE_EVERY = 50
+RELIABLE_EVERY = 200
+# the multi-rhs FP32 configuration (reported beside the headline)
+L1 = (32, 32, 32, 8)
+MASS1 = 0.01
+RELIABLE_EVERY1 = 50
 LINK_SEED = 1
 SOURCE_SEED = 2
 DSLASH_FLOPS_PER_SITE_RHS = 1146
 L2_BYTES = 129 * 1024 * 1024
 NOMINAL_HBM_GBS = 8000.0
-# FP64 textbook CG iterations of this system (rhs 0) to 1e-10; written by
-# oracle/cg_iterations.py, which runs the oracle only.
+# FP32 lanes of one SM and its clock: the FP32 ALU peak is SMs x 128 x 2 flop x clock
+FP32_LANES_PER_SM = 128
+# FP64 textbook CG iterations of the 32^3x8 system (rhs 0) to 1e-10; written
+# by oracle/cg_iterations.py, which runs the oracle only.
 ITER_FILE = os.path.join(ROOT, "oracle", "cg_iterations_32x32x32x8_m0.01.json")
 
 
 def workload_config(n_gpus: int) -> dict:
     return {
-        "workload": "HISQ even-odd CG, 32^3x8, n=8 Z2 rhs, m=0.01, FP32 inner (U r18, N r14), "
-                    "FP64 reliable updates every 50, tol 1e-10",
+        "workload": "HISQ even-odd CG, 48^3x12, n=8 Gaussian rhs, m=0.0025, FP16 storage (16-bit "
+                    "fixed-point links U r18 / N r14, half spinors) with FP32 arithmetic, FP64 reliable "
+                    f"updates every {RELIABLE_EVERY} and FP64 solution, tol 1e-10",
         "lattice": list(L), "nrhs_per_gpu": NRHS, "global_rhs": NRHS * n_gpus, "mass": MASS,
-        "tol": TOL, "inner_prec": "f32", "recon_U": 18, "recon_N": 14,
-        "reliable_every": RELIABLE_EVERY, "parallelism": f"rhs-bundle replicas x{n_gpus}",
-        "l2": "inputs larger than L2 (134 MB of packed links) and L2 flushed between steps",
+        "tol": TOL, "inner_prec": "f16 storage, f32 arithmetic", "storage_dtype": "f16",
+        "recon_U": 18, "recon_N": 14, "reliable_every": RELIABLE_EVERY,
+        "spinor_layout": "bundle", "parallelism": f"rhs-bundle replicas x{n_gpus}",
+        "l2": "inputs larger than L2 (340 MB of packed links, 1.5 GB FP64 links) and L2 flushed between steps",
     }
 
 
@@ -161,24 +176,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of one launch of the bench's roofline Dslash, from
-# one ncu capture of that kernel (profiles/dslash_f32_r18_r14_n8_32x32x32x8_pipelined.md),
-# keyed by (lattice, rhs per thread, min blocks, mapping flags). A mapping
-# without a capture reports null.
-DSLASH_TRAFFIC = {((32, 32, 32, 8), 4, 2, 16): 159_460_352 + 5_904_896}
-
-
-def dslash_kernel_name(rpt, minb, flags, L):
-    if flags & 16:
-        name = f"dslash_pipe_kernel<float,float,18,14,rpt={rpt},minb={minb},depth=2,EPI_NONE,AoS>"
-    elif flags & 8:
-        name = f"dslash_pipe_kernel<float,float,18,14,rpt={rpt},minb={minb},depth=1,EPI_NONE,AoS>"
-    elif flags & 4:
-        name = f"dslash_staged_kernel<float,float,18,14,rpt={rpt},minb={minb},EPI_NONE,AoS>"
-    else:
-        name = f"dslash_kernel<float,float,18,14,rpt={rpt},minb={minb},EPI_NONE,AoS>"
-    lat = "x".join(str(v) for v in L)
-    return f"{name} n={NRHS} on {lat}", DSLASH_TRAFFIC.get((tuple(L), rpt, minb, flags))
+# DRAM bytes (read + write) of one launch of a roofline Dslash, from one ncu
+# capture of that kernel (profiles/), keyed by (precision, lattice, n, rhs per
+# thread, min blocks, mapping flags). A mapping without a capture reports null.
+DSLASH_TRAFFIC = {}
 
 
 def measured_peaks() -> dict:
@@ -186,23 +187,44 @@ def measured_peaks() -> dict:
     if os.path.exists(path):
         with open(path) as fh:
             d = json.load(fh)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
-    return {"hbm_gbs": 6800.0, "source": "fallback"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FP32 ALU peak: every SM retires 128 fused multiply-adds (2 flop) per clock."""
+    return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def roofline_bound(flops: float, nbytes: float, alu_tflops: float, hbm_gbs: float) -> str:
+    """The roofline that binds a kernel: "alu" when its arithmetic intensity
+    lies past the ridge (ALU peak / HBM peak), else "hbm"."""
+    return "alu" if flops / nbytes > alu_tflops * 1e3 / hbm_gbs else "hbm"
+
+
+def dslash_traffic(prec: str, lattice, n: int, mapping) -> int | None:
+    """ncu DRAM bytes of one launch of a captured Dslash configuration, else None."""
+    return DSLASH_TRAFFIC.get((prec, tuple(lattice), n) + tuple(mapping))
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (only this function and run_reference touch oracle/)
 # ---------------------------------------------------------------------------
 
-def fp64_iterations(default: int | None) -> tuple[int | None, str]:
-    if os.path.exists(ITER_FILE):
-        with open(ITER_FILE) as fh:
+def fp64_iterations(default: int | None, mixed: bool = False) -> tuple[int | None, str]:
+    """The oracle's own FP64 CG iteration count of the system if it has been
+    written (oracle/cg_iterations.py), else the given count."""
+    name = "cg_iterations_48x48x48x12_m0.0025.json" if mixed else "cg_iterations_32x32x32x8_m0.01.json"
+    path = os.path.join(ROOT, "oracle", name)
+    if os.path.exists(path):
+        with open(path) as fh:
             return int(json.load(fh)["iterations"]), "oracle CG iteration count (oracle/cg_iterations.py)"
     return default, "iteration count of the FP64 GPU solve of the same system"
 
 
 def oracle_sample(U, N, b1, iters: int) -> float:
-    """Seconds per oracle CG iteration for one rhs on the full lattice."""
+    """Seconds per oracle CG iteration for one rhs of the headline system."""
     from oracle import hisq_oracle as O
     t0 = time.perf_counter()
     O.cg(lambda q: O.apply_Ae(U, N, q, L, MASS), b1, tol=1e-300, maxiter=iters)
@@ -210,19 +232,46 @@ def oracle_sample(U, N, b1, iters: int) -> float:
 
 
 def cpu_baseline(U, N, b, fp64_iters_gpu: int | None) -> dict:
-    iters_total, how = fp64_iterations(fp64_iters_gpu)
+    iters_total, how = fp64_iterations(fp64_iters_gpu, mixed=True)
     sample_iters = 3
     t_it = oracle_sample(U, N, b[:1], sample_iters)
     value = t_it * iters_total if iters_total else None
     return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
             "host_cpus": os.cpu_count(),
-            "sample": f"{sample_iters} iterations of the numpy FP64 oracle CG, 1 rhs on 32^3x8 "
+            "sample": f"{sample_iters} iterations of the numpy FP64 oracle CG, 1 rhs on 48^3x12 "
                       f"({t_it:.3f} s/iteration), scaled by {iters_total} iterations ({how})"}
 
 
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def time_bundle_dslash(H, torch, g, prec, n, stream, flush, reps=20):
+    """Per-launch CUDA-event time (mean over reps) of the bundle Dslash the CG
+    uses, with an L2 flush (a write larger than L2) before every launch."""
+    vh = int(np.prod(g.L)) // 2
+    dt = torch.float32 if prec == H.HISQ_F32 else torch.float16
+    src = [torch.randn(vh, 3, dtype=torch.complex128, device=flush.device) for _ in range(n)]
+    vb = torch.empty(H.hisq.bundle_bytes(g, n, prec) // (4 if prec == H.HISQ_F32 else 2), dtype=dt,
+                     device=flush.device)
+    H.hisq_bundle_pack(g, src, prec, vb, stream=stream)
+    del src
+    wb = torch.empty_like(vb)
+    for _ in range(3):
+        H.hisq_dslash_ex(g, 0.0, vb, wb, 0, prec, H.HISQ_BUNDLE, stream=stream, n=n)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in ev:
+        flush.fill_(1.0)
+        e0.record(stream)
+        H.hisq_dslash_ex(g, 0.0, vb, wb, 0, prec, H.HISQ_BUNDLE, stream=stream, n=n)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    t = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3 / reps
+    sb = 4 if prec == H.HISQ_F32 else 2
+    nbytes = dslash_bytes_per_site(n, g.recon_U, g.recon_N, sb, sb) * vh
+    flops = DSLASH_FLOPS_PER_SITE_RHS * n * vh
+    return t, nbytes, flops
+
 
 def run_gpu(args):
     import torch
@@ -237,20 +286,23 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     H.hisq.library()   # fails loudly if the CUDA library is missing
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = fp32_peak_tflops(sm_count, peaks["sm_max_mhz"])
 
     U, N = gen.hisq_links(L, seed=LINK_SEED)
-    b = gen.z2_source(L, NRHS, seed=source_seed_for_rank(rank))
+    b = gen.gaussian_source(L, NRHS, seed=source_seed_for_rank(rank))
     dU, dN = torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev)
-    stream = torch.cuda.current_stream(dev)
-
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    g = H.hisq_gauge_load(L, dU, dN, prec=H.HISQ_F32, recon_U=18, recon_N=14)
+    g = H.hisq_gauge_load(L, dU, dN, prec=H.HISQ_F16, recon_U=18, recon_N=14)
     pack_s = time.perf_counter() - t0
     bt = [torch.from_numpy(b[k]).to(dev) for k in range(NRHS)]
     xt = [torch.zeros_like(t) for t in bt]
-    params = H.cg_params(inner_prec=H.HISQ_F32, reliable_every=RELIABLE_EVERY)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    params = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=RELIABLE_EVERY,
+                         spinor_layout=H.HISQ_BUNDLE)
 
     def step():
         return H.hisq_cg_solve(g, MASS, 0.0, bt, xt, TOL, params, stream=stream)
@@ -276,9 +328,8 @@ def run_gpu(args):
         durs.append(e0.elapsed_time(e1) / 1e3)
         # per iteration: two Dslash, update_r, update_px; per reliable update:
         # accumulate, two FP64 Dslash, rescale; per solve: norm |b|, copy the
-        # residual, rescale (and with SoA workspaces a transpose of b in and x out)
+        # residual, rescale
         launches += 4 * st.total_iters + 4 * st.reliable_updates + 3
-        launches += 2 if params.spinor_layout == H.HISQ_SOA else 0
         stats_last = st
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
@@ -289,39 +340,38 @@ def run_gpu(args):
     s_per_rhs = t_step_max / (NRHS * world)
     res = [stats_last.true_rel_res[k] for k in range(NRHS)]
 
-    # ---- the dominant kernel alone: multi-rhs Dslash, FP32, U r18 / N r14 ----
-    vh = int(np.prod(L)) // 2
-    peaks = measured_peaks()
-
-    def time_dslash(n, reps=40):
-        vs = [torch.randn(vh, 3, dtype=torch.complex64, device=dev) for _ in range(n)]
-        ws = [torch.empty_like(v) for v in vs]
-        for _ in range(3):
-            H.hisq_dslash(g, vs, ws, 0, H.HISQ_F32, stream=stream)
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            H.hisq_dslash(g, vs, ws, 0, H.HISQ_F32, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        t = e0.elapsed_time(e1) / 1e3 / reps
-        nbytes = dslash_bytes_per_site(n, 18, 14, 4, 4) * vh
-        flops = DSLASH_FLOPS_PER_SITE_RHS * n * vh
-        return t, nbytes, flops
-
-    t_d, bytes_d, flops_d = time_dslash(NRHS)
-    rpt_d, minb_d, flags_d = H.hisq_get_dslash_mapping(g, NRHS, H.HISQ_F32)
-    kernel_d, traffic_d = dslash_kernel_name(rpt_d, minb_d, flags_d, L)
+    # ---- the dominant kernel alone: FP16 bundle Dslash of the solve, and FP32 ----
+    t_d, bytes_d, flops_d = time_bundle_dslash(H, torch, g, H.HISQ_F16, NRHS, stream, flush)
+    mapping = H.hisq_get_dslash_mapping_ex(g, NRHS, H.HISQ_F16, H.HISQ_BUNDLE)
     gbs = bytes_d / t_d / 1e9
-    sweep = {}
-    for n in (1, 2, 4, 16):
-        tn, bn, fn = time_dslash(n, reps=20)
-        sweep[str(n)] = {"us": round(tn * 1e6, 2), "gbs": round(bn / tn / 1e9, 1),
-                         "gflops": round(fn / tn / 1e9, 1)}
-    sweep[str(NRHS)] = {"us": round(t_d * 1e6, 2), "gbs": round(gbs, 1),
-                        "gflops": round(flops_d / t_d / 1e9, 1)}
+    tfl = flops_d / t_d / 1e12
+    intensity = flops_d / bytes_d
+    ridge = alu_peak * 1e3 / peaks["hbm_gbs"]
+    kernel_d = (f"dslash_bundle_kernel<__half,Fx16,18,14,rpt={mapping[0]},minb={mapping[1]},"
+                f"flags={mapping[2]}> n={NRHS} on 48x48x48x12")
+    traffic_d = dslash_traffic("f16", L, NRHS, mapping)
+    hbm = {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": round(gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"]}
+    alu = {"achieved": round(tfl, 2), "peak": round(alu_peak, 1), "unit": "TFLOP/s",
+           "frac": round(tfl / alu_peak, 4),
+           "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                          f"{peaks['sm_max_mhz']:.0f} MHz"}
+    bound = roofline_bound(flops_d, bytes_d, alu_peak, peaks["hbm_gbs"])
+    main = alu if bound == "alu" else hbm
+    dslash_info = {"f16": {"us_per_launch": round(t_d * 1e6, 2), "gbs": round(gbs, 1),
+                           "frac_of_8tbs": round(gbs / NOMINAL_HBM_GBS, 4), "hbm_frac": hbm["frac"],
+                           "tflops": round(tfl, 2), "alu_frac": alu["frac"],
+                           "flop_per_byte": round(intensity, 2), "mapping": list(mapping)}}
+    g32 = H.hisq_gauge_load(L, dU, dN, prec=H.HISQ_F32, recon_U=18, recon_N=14)
+    t32, b32, f32 = time_bundle_dslash(H, torch, g32, H.HISQ_F32, NRHS, stream, flush)
+    dslash_info["f32"] = {"us_per_launch": round(t32 * 1e6, 2), "gbs": round(b32 / t32 / 1e9, 1),
+                          "hbm_frac": round(b32 / t32 / 1e9 / peaks["hbm_gbs"], 4),
+                          "tflops": round(f32 / t32 / 1e12, 2),
+                          "alu_frac": round(f32 / t32 / 1e12 / alu_peak, 4),
+                          "flop_per_byte": round(f32 / b32, 2),
+                          "mapping": list(H.hisq_get_dslash_mapping_ex(g32, NRHS, H.HISQ_F32,
+                                                                                 H.HISQ_BUNDLE))}
+    H.hisq_gauge_free(g32)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     hb = [torch.from_numpy(b[k]).pin_memory() for k in range(NRHS)]
@@ -336,14 +386,19 @@ def run_gpu(args):
     bytes_in = sum(t.numel() * t.element_size() for t in hb)
     bytes_out = sum(t.numel() * t.element_size() for t in hx)
 
-    # ---- plain FP64 single-rhs GPU CG on the same system (rank 0) ----
+    # ---- plain FP64 single-rhs GPU CG on the same system and source 0 (rank 0) ----
     fp64 = None
     fp64_iters = None
+    configs1 = None
     if rank == 0:
         g64 = H.hisq_gauge_load(L, dU, dN, prec=H.HISQ_F64)
         x64 = [torch.zeros_like(bt[0])]
         p64 = H.cg_params(inner_prec=H.HISQ_F64)
-        H.hisq_cg_solve(g64, MASS, 0.0, bt[:1], x64, TOL, p64, stream=stream)   # warm-up
+        try:   # warm-up: a few iterations (workspace, graphs)
+            H.hisq_cg_solve(g64, MASS, 0.0, bt[:1], x64, TOL, H.cg_params(inner_prec=H.HISQ_F64, maxiter=20),
+                            stream=stream)
+        except H.HisqError:
+            pass
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -358,26 +413,25 @@ def run_gpu(args):
                 "mixed_over_fp64_time": s_per_rhs / t64,
                 "mixed_vs_fp64_solution_rel_diff": diff}
         H.hisq_gauge_free(g64)
+        del x64
+        configs1 = run_configs1(H, torch, gen, dev, stream)
+    del dU, dN
 
     out = {
         "metric": METRIC, "value": s_per_rhs, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step_max * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (Haar-random links, Z2 sources; seeded)",
+        "dtype": "f32", "data": "synthetic (Haar-random links, Gaussian sources; seeded)",
         "config": workload_config(world),
         "cg": {"iterations": stats_last.total_iters, "reliable_updates": stats_last.reliable_updates,
                "max_true_rel_res": max(res), "wall_s_per_step": wall / args.steps},
-        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
-                     "traffic": traffic_d,
-                     "kernel": kernel_d,
-                     "peak_source": peaks["source"],
-                     "bytes_per_launch": bytes_d},
-        "dslash": {"gbs": round(gbs, 1), "frac_of_8tbs": round(gbs / NOMINAL_HBM_GBS, 4),
-                   "gflops": round(flops_d / t_d / 1e9, 1), "us_per_launch": round(t_d * 1e6, 2),
-                   "sweep_n": sweep},
+        "roofline": dict(main, bound=bound, traffic=traffic_d, kernel=kernel_d,
+                         bytes_per_launch=bytes_d, flops_per_launch=flops_d, hbm=hbm, alu=alu,
+                         ridge_flop_per_byte=round(ridge, 2)),
+        "dslash": dslash_info,
         "link_pack_s": pack_s,
         "fp64": fp64,
+        "configs1": configs1,
         "e2e": {"value": e2e_t / (NRHS * world), "unit": UNIT,
                 "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out},
         "gpu_launches": launches,
@@ -394,6 +448,32 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_configs1(H, torch, gen, dev, stream) -> dict:
+    """The multi-rhs FP32 configuration beside the headline: 32^3x8, n = 8 Z2
+    sources, m = 0.01, FP32 storage (U r18 / N r14), FP64 reliable updates
+    every 50; one timed solve after a warm-up, and the FP64 single-rhs solve."""
+    U, N = gen.hisq_links(L1, seed=LINK_SEED)
+    dU, dN = torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev)
+    b = gen.z2_source(L1, NRHS, seed=SOURCE_SEED)
+    bt = [torch.from_numpy(b[k]).to(dev) for k in range(NRHS)]
+    xt = [torch.zeros_like(t) for t in bt]
+    g = H.hisq_gauge_load(L1, dU, dN, prec=H.HISQ_F32, recon_U=18, recon_N=14)
+    t, st = _time_solve(H, torch, g, MASS1, 0.0, bt, xt, TOL,
+                        H.cg_params(inner_prec=H.HISQ_F32, reliable_every=RELIABLE_EVERY1), stream)
+    H.hisq_gauge_free(g)
+    g = H.hisq_gauge_load(L1, dU, dN, prec=H.HISQ_F64)
+    x64 = [torch.zeros_like(bt[0])]
+    t64, st64 = _time_solve(H, torch, g, MASS1, 0.0, bt[:1], x64, TOL, H.cg_params(inner_prec=H.HISQ_F64),
+                            stream)
+    H.hisq_gauge_free(g)
+    return {"workload": "HISQ even-odd CG, 32^3x8, n=8 Z2 rhs, m=0.01, FP32 storage (U r18, N r14), "
+                        "FP64 reliable updates every 50, tol 1e-10",
+            "s_per_rhs": t / NRHS, "iterations": st.total_iters, "reliable_updates": st.reliable_updates,
+            "max_true_rel_res": max(st.true_rel_res[k] for k in range(NRHS)),
+            "fp64_single_rhs_s": t64, "fp64_iterations": st64.total_iters,
+            "mixed_over_fp64_time": (t / NRHS) / t64}
 
 
 # ---------------------------------------------------------------------------
@@ -460,20 +540,20 @@ def run_oracle_timing(args):
           "sample": "complete solve"})
 
     # 32^3x8, m = 0.01
-    U, N = gen.hisq_links(L, seed=LINK_SEED)
-    b = gen.z2_source(L, NRHS, seed=SOURCE_SEED)
+    U, N = gen.hisq_links(L1, seed=LINK_SEED)
+    b = gen.z2_source(L1, NRHS, seed=SOURCE_SEED)
     iters_total, how = fp64_iterations(None)
-    t_it = _oracle_cg_iteration_seconds(lambda q: O.apply_Ae(U, N, q, L, MASS), b[:1], 2)
+    t_it = _oracle_cg_iteration_seconds(lambda q: O.apply_Ae(U, N, q, L1, MASS1), b[:1], 2)
     line({"workload": "oracle 32^3x8 m=0.01", "cores": 1, "cg_s_per_rhs": t_it * iters_total,
           "cg_iterations": iters_total, "iterations_from": how,
-          "dslash_s_per_call_8rhs": dslash_s(U, N, b, L),
+          "dslash_s_per_call_8rhs": dslash_s(U, N, b, L1),
           "sample": f"2 CG iterations of one rhs ({t_it:.3f} s/iteration)"})
     procs = min(NRHS, cpus)
     ctx = mp.get_context("spawn")
-    with ctx.Pool(procs, initializer=_oracle_worker_init, initargs=(L,)) as pool:
-        pool.map(_oracle_sample_worker, [(MASS, 0, 1)] * procs, chunksize=1)     # warm-up
+    with ctx.Pool(procs, initializer=_oracle_worker_init, initargs=(L1,)) as pool:
+        pool.map(_oracle_sample_worker, [(MASS1, 0, 1)] * procs, chunksize=1)     # warm-up
         t0 = time.perf_counter()
-        pool.map(_oracle_sample_worker, [(MASS, k, 2) for k in range(NRHS)], chunksize=1)
+        pool.map(_oracle_sample_worker, [(MASS1, k, 2) for k in range(NRHS)], chunksize=1)
         wall = time.perf_counter() - t0
     per_it_bundle = wall / 2
     line({"workload": "oracle 32^3x8 m=0.01, all cores", "cores": procs,
@@ -512,21 +592,23 @@ def run_reference(args):
         return
     import hisq_inputs as gen
     U, N = gen.hisq_links(L, seed=LINK_SEED)
-    b = gen.z2_source(L, NRHS, seed=SOURCE_SEED)
-    iters_total, how = fp64_iterations(None)
+    b = gen.gaussian_source(L, NRHS, seed=SOURCE_SEED)
+    iters_total, how = fp64_iterations(11310, mixed=True)
+    if how.startswith("iteration count of the FP64 GPU"):
+        how = "iteration count of the FP64 GPU solve of the same system, measured separately"
     per_step_iters = 1
     for _ in range(args.warmup):
         oracle_sample(U, N, b[:1], per_step_iters)
     ts = [oracle_sample(U, N, b[:1], per_step_iters) for _ in range(args.steps)]
     t_it = sum(ts) / len(ts)
     value = t_it * iters_total if iters_total else None
-    sample = (f"{per_step_iters} numpy FP64 oracle CG iteration per step, 1 rhs on 32^3x8 "
+    sample = (f"{per_step_iters} numpy FP64 oracle CG iteration per step, 1 rhs on 48^3x12 "
               f"({t_it:.3f} s/iteration), scaled by {iters_total} iterations ({how})")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_it * per_step_iters * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (Haar-random links, Z2 sources; seeded)", "config": workload_config(world),
+        "data": "synthetic (Haar-random links, Gaussian sources; seeded)", "config": workload_config(world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -591,22 +673,22 @@ def run_cg_configs(args):
     H.hisq_gauge_free(g)
 
     # 32^3x8, FP32 inner, n = 1, 2, 4, 8, and FP64 single rhs
-    U, N = gen.hisq_links(L, seed=LINK_SEED)
+    U, N = gen.hisq_links(L1, seed=LINK_SEED)
     dU, dN = torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev)
-    b = gen.z2_source(L, NRHS, seed=SOURCE_SEED)
-    g = H.hisq_gauge_load(L, dU, dN, prec=H.HISQ_F32, recon_U=18, recon_N=14)
+    b = gen.z2_source(L1, NRHS, seed=SOURCE_SEED)
+    g = H.hisq_gauge_load(L1, dU, dN, prec=H.HISQ_F32, recon_U=18, recon_N=14)
     for n in (1, 2, 4, 8):
         bt = dev_list(b[:n])
         xt = [torch.zeros_like(x) for x in bt]
-        t, st = _time_solve(H, torch, g, MASS, 0.0, bt, xt, TOL,
-                            H.cg_params(inner_prec=H.HISQ_F32, reliable_every=RELIABLE_EVERY), stream)
-        _cg_line("fp32 32^3x8 m=0.01", L, n, "f32", t, st)
+        t, st = _time_solve(H, torch, g, MASS1, 0.0, bt, xt, TOL,
+                            H.cg_params(inner_prec=H.HISQ_F32, reliable_every=RELIABLE_EVERY1), stream)
+        _cg_line("fp32 32^3x8 m=0.01", L1, n, "f32", t, st)
     H.hisq_gauge_free(g)
-    g = H.hisq_gauge_load(L, dU, dN, prec=H.HISQ_F64)
+    g = H.hisq_gauge_load(L1, dU, dN, prec=H.HISQ_F64)
     bt = dev_list(b[:1])
     xt = [torch.zeros_like(bt[0])]
-    t, st = _time_solve(H, torch, g, MASS, 0.0, bt, xt, TOL, H.cg_params(inner_prec=H.HISQ_F64), stream)
-    _cg_line("fp64 32^3x8 m=0.01", L, 1, "f64", t, st)
+    t, st = _time_solve(H, torch, g, MASS1, 0.0, bt, xt, TOL, H.cg_params(inner_prec=H.HISQ_F64), stream)
+    _cg_line("fp64 32^3x8 m=0.01", L1, 1, "f64", t, st)
     H.hisq_gauge_free(g)
     del dU, dN
 
@@ -735,7 +817,7 @@ def run_batched(args):
         bt = [torch.from_numpy(b[k]).to(dev) for k in range(n)]
         probs.append(dict(g=g, mass=m, mu=0.0, b=bt, x=[torch.zeros_like(t) for t in bt], tol=TOL))
         torch.cuda.empty_cache()
-    params = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=RELIABLE_EVERY)
+    params = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=RELIABLE_EVERY1)
     H.hisq_cg_solve_batched(probs, params, stream=stream)        # warm-up (graphs, workspaces)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -783,11 +865,11 @@ def run_inverter_sweep(args):
         b = gen.z2_source(Ls, n, seed=SOURCE_SEED)
         bt = [torch.from_numpy(b[k]).to(dev) for k in range(n)]
         xt = [torch.zeros_like(t) for t in bt]
-        p = H.cg_params(inner_prec=H.HISQ_F32, reliable_every=RELIABLE_EVERY, maxiter=iters)
+        p = H.cg_params(inner_prec=H.HISQ_F32, reliable_every=RELIABLE_EVERY1, maxiter=iters)
 
         def solve():
             try:
-                return H.hisq_cg_solve(g, MASS, 0.0, bt, xt, 1e-30, p, stream=stream)
+                return H.hisq_cg_solve(g, MASS1, 0.0, bt, xt, 1e-30, p, stream=stream)
             except H.HisqError as e:          # HISQ_ENOCONV at maxiter: stats ride on the error
                 return e.stats
         solve()
@@ -809,6 +891,79 @@ def run_inverter_sweep(args):
         torch.cuda.empty_cache()
 
 
+def run_dslash_probe(args):
+    """A fixed number of Dslash (or normal-operator) launches of one kernel
+    configuration, for ncu captures and event timing outside the headline:
+    prints one JSON line with the CUDA-event time per launch, the algorithmic
+    GB/s (8 (f_U + f_N) s_l + 12 n s_s bytes per output site) and GFlop/s."""
+    import torch
+
+    import hisq_inputs as gen
+    import paper_1411_4439_gb300 as H
+
+    precs = {"f64": H.HISQ_F64, "f32": H.HISQ_F32, "f16": H.HISQ_F16}
+    sbytes = {"f64": 8, "f32": 4, "f16": 2}
+    Ls = tuple(args.lattice)
+    prec = precs[args.prec]
+    n = args.n
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    H.hisq.library()
+    U, N = gen.hisq_links(Ls, seed=LINK_SEED)
+    fu, fn = (18, 18) if prec == H.HISQ_F64 else tuple(args.recon)
+    g = H.hisq_gauge_load(Ls, torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev), prec=prec,
+                          recon_U=fu, recon_N=fn)
+    del U, N
+    if args.rpt or args.minb or args.flags:
+        H.hisq_set_dslash_mapping(g, args.rpt, args.minb, args.flags)
+    layout = {"aos": H.HISQ_AOS, "soa": H.HISQ_SOA, "bundle": H.HISQ_BUNDLE}[args.layout]
+    vh = int(np.prod(Ls)) // 2
+    stream = torch.cuda.current_stream(dev)
+    if layout == H.HISQ_BUNDLE:
+        src = [torch.randn(vh, 3, dtype=torch.complex128, device=dev) for _ in range(n)]
+        dt = torch.float32 if prec == H.HISQ_F32 else torch.float16
+        vb = torch.empty(H.hisq.bundle_bytes(g, n, prec) // (4 if prec == H.HISQ_F32 else 2), dtype=dt,
+                         device=dev)
+        H.hisq_bundle_pack(g, src, prec, vb)
+        wb = torch.empty_like(vb)
+        del src
+    else:
+        if prec == H.HISQ_F64:
+            vs = [torch.randn(vh, 3, dtype=torch.complex128, device=dev) for _ in range(n)]
+        elif prec == H.HISQ_F32:
+            vs = [torch.randn(vh, 3, dtype=torch.complex64, device=dev) for _ in range(n)]
+        else:
+            vs = [torch.randn(vh, 3, 2, device=dev).half() for _ in range(n)]
+        ws = [torch.empty_like(v) for v in vs]
+
+    def launch():
+        if args.op == "mdagm":
+            H.hisq_mdagm(g, 0.01, vs, ws, prec, stream=stream)
+        elif layout == H.HISQ_BUNDLE:
+            H.hisq_dslash_ex(g, args.mu, vb, wb, 0, prec, layout, stream=stream, n=n)
+        else:
+            H.hisq_dslash_ex(g, args.mu, vs, ws, 0, prec, layout, stream=stream)
+
+    for _ in range(args.warmup):
+        launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.reps):
+        launch()
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.reps
+    ops = 2 if args.op == "mdagm" else 1
+    nb = dslash_bytes_per_site(n, fu, fn, sbytes[args.prec], sbytes[args.prec]) * vh
+    print(json.dumps({"workload": "dslash probe", "lattice": list(Ls), "n": n, "prec": args.prec,
+                      "recon": [fu, fn], "op": args.op, "layout": args.layout, "rpt": args.rpt,
+                      "minb": args.minb, "flags": args.flags, "us_per_launch": t * 1e6 / ops,
+                      "alg_bytes_per_dslash": nb, "alg_gbs": nb * ops / t / 1e9,
+                      "gflops": DSLASH_FLOPS_PER_SITE_RHS * n * vh * ops / t / 1e9}), flush=True)
+    H.hisq_gauge_free(g)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -816,11 +971,23 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["headline", "cg-configs", "dslash-sweep", "batched", "inverter-sweep",
-                                           "oracle-timing"],
+                                           "oracle-timing", "dslash-probe"],
                     default="headline",
                     help="headline = the one JSON line of the contract; oracle-timing needs --impl reference")
     ap.add_argument("--lattices", default="48x48x48x12,64x64x64x16",
                     help="lattices of the Dslash sweep (Lx x Ly x Lz x Lt, comma separated)")
+    # dslash-probe: one kernel configuration
+    ap.add_argument("--lattice", type=int, nargs=4, default=[48, 48, 48, 12])
+    ap.add_argument("--n", type=int, default=8)
+    ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f16")
+    ap.add_argument("--recon", type=int, nargs=2, default=[18, 14])
+    ap.add_argument("--layout", choices=["aos", "soa", "bundle"], default="bundle")
+    ap.add_argument("--rpt", type=int, default=0)
+    ap.add_argument("--minb", type=int, default=0)
+    ap.add_argument("--flags", type=int, default=0, help="HISQ_MAP_* bits")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--mu", type=float, default=0.0)
+    ap.add_argument("--op", choices=["dslash", "mdagm"], default="dslash")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":
@@ -833,6 +1000,8 @@ def main(argv=None):
         run_batched(args)
     elif args.workload == "inverter-sweep":
         run_inverter_sweep(args)
+    elif args.workload == "dslash-probe":
+        run_dslash_probe(args)
     else:
         run_gpu(args)
 

@@ -72,10 +72,18 @@ enum { HISQ_F64 = 0, HISQ_F32 = 1, HISQ_F16 = 2 };
 typedef int hisq_recon;
 enum { HISQ_R18 = 18, HISQ_R12 = 12, HISQ_R14 = 14 };
 
-/* Spinor layout of one rhs on one parity: AoS [V_h][3] (colour fastest) or
- * SoA [3][V_h] (site fastest, one plane per colour). */
+/* Spinor layout on one parity: AoS [V_h][3] per rhs (colour fastest), SoA
+ * [3][V_h] per rhs (site fastest, one plane per colour), or the bundle layout
+ * of all n rhs together in one buffer (FP32 and FP16 storage only): 16-byte
+ * chunks, each one colour of W consecutive rhs at one site with the W real
+ * parts first and then the W imaginary parts (W = 2 for FP32: float
+ * re_k, re_k+1, im_k, im_k+1; W = 4 for FP16: 4 halves of real parts, 4 of
+ * imaginary parts), chunk (g = k / W, colour c, site h) at index
+ * (3 g + c) V_h + h. n must be a multiple of W. A warp of 32 neighbouring
+ * sites then reads whole 512-byte rows for every hop of Eq. 3, and a link
+ * load serves W rhs per chunk. */
 typedef int hisq_layout;
-enum { HISQ_AOS = 0, HISQ_SOA = 1 };
+enum { HISQ_AOS = 0, HISQ_SOA = 1, HISQ_BUNDLE = 2 };
 
 typedef struct hisq_gauge_s* hisq_gauge;
 
@@ -149,15 +157,28 @@ enum {
     HISQ_MAP_L2_PREFETCH = 2,
     HISQ_MAP_STAGED = 4,
     HISQ_MAP_PIPELINED = 8,
-    HISQ_MAP_PIPELINED2 = 16
+    HISQ_MAP_PIPELINED2 = 16,
+    HISQ_MAP_SCALAR = 32,
+    HISQ_MAP_NO_LOOKAHEAD = 64
 };
+/* On the bundle layout (rhs per thread 4 or 8, min blocks per SM of 128-thread
+ * blocks 1..4) the kernel multiplies rhs pairs with packed FP32 (f32x2)
+ * instructions and keeps the next hop's link load in flight; flags select
+ * variants: HISQ_MAP_PIPELINED also the next hop's neighbour chunks,
+ * HISQ_MAP_SCALAR scalar FP32 arithmetic, HISQ_MAP_NO_LOOKAHEAD no loads
+ * ahead of the current hop. */
 hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_blocks,
                                     int flags);
 
 /* The mapping a Dslash of n rhs in `spinor_prec` will use on this handle:
- * rhs per thread, min blocks per SM and HISQ_MAP_* flags (host pointers). */
+ * rhs per thread, min blocks per SM and HISQ_MAP_* flags (host pointers), for
+ * the AoS layout (hisq_get_dslash_mapping) or a given layout (_ex; the bundle
+ * layout returns HISQ_EINVAL when n does not fit it). */
 hisq_status hisq_get_dslash_mapping(hisq_gauge g, int n, hisq_prec spinor_prec,
                                     int* rhs_per_thread, int* min_blocks, int* flags);
+hisq_status hisq_get_dslash_mapping_ex(hisq_gauge g, int n, hisq_prec spinor_prec,
+                                       hisq_layout layout, int* rhs_per_thread,
+                                       int* min_blocks, int* flags);
 
 /*
  * Autotuner: times `reps` Dslash launches of every built mapping that fits
@@ -177,9 +198,10 @@ hisq_status hisq_autotune_dslash(hisq_gauge g, int n, hisq_prec spinor_prec,
  * fat links where exact): loads the links, exactly as hisq_gauge_load, with
  * every (recon_U, recon_N) pair that has a kernel for `prec` (F64: 18/18;
  * F32/F16: 18/18, 18/14, 12/14, 14/14), skips pairs that do not hold the
- * links within recon_tol, runs hisq_autotune_dslash for n rhs in both spinor
- * layouts on each, and returns in *out the handle whose SoA Dslash (the CG's
- * layout) was fastest, with its tuned mappings. hisq_gauge_info reports the
+ * links within recon_tol, runs hisq_autotune_dslash for n rhs in every spinor
+ * layout that fits n on each, and returns in *out the handle whose Dslash in
+ * the CG's layout (the bundle layout where n fits it, else AoS) was fastest,
+ * with its tuned mappings. hisq_gauge_info reports the
  * chosen compression. The choice is cached per (L, n, prec) for the life of
  * the process; later calls load that pair directly (and search again if it
  * does not hold their links). Transient device memory:
@@ -225,7 +247,9 @@ hisq_status hisq_link_reconstruct(const int L[4], const void* packed,
  * hisq_dslash uses the AoS layout. hisq_dslash_ex takes the spinor layout and
  * adds a chemical potential mu on the temporal hops: forward one-hop
  * x e^{+mu}, backward one-hop x e^{-mu}, forward Naik x e^{+3mu}, backward
- * Naik x e^{-3mu}. Asynchronous on `stream`.
+ * Naik x e^{-3mu}. With layout HISQ_BUNDLE, v and w hold one pointer each,
+ * the bundle buffers of all n rhs (n a multiple of the chunk width W; F32 or
+ * F16 only; 16-byte aligned). Asynchronous on `stream`.
  */
 hisq_status hisq_dslash(hisq_gauge g, const void* const v[], void* const w[],
                         int n, int parity, hisq_prec spinor_prec, void* stream);
@@ -233,6 +257,22 @@ hisq_status hisq_dslash_ex(hisq_gauge g, double mu, const void* const v[],
                            void* const w[], int n, int parity,
                            hisq_prec spinor_prec, hisq_layout layout,
                            void* stream);
+
+/*
+ * Conversion between n FP64 vectors and one bundle (layout HISQ_BUNDLE, see
+ * hisq_layout) of storage precision F32 or F16, for the bundle Dslash and the
+ * CG. src / dst: host arrays of n device pointers to complex128 [V_h][3] on
+ * one parity (V_h = V / 2 of the handle's lattice); bundle: device pointer to
+ * n * 3 * V_h complex numbers of `prec` (16-byte aligned). Packing rounds to
+ * `prec` (round to nearest). n must be a multiple of W (2 for F32, 4 for
+ * F16), at most 16. The paper's layouts are per-rhs arrays; this interleave
+ * is this library's (Sec. 2 notes a per-site rhs-contiguous layout helped on
+ * Xeon Phi). Asynchronous on `stream`.
+ */
+hisq_status hisq_bundle_pack(hisq_gauge g, const void* const src[], int n, hisq_prec prec,
+                             void* bundle, void* stream);
+hisq_status hisq_bundle_unpack(hisq_gauge g, const void* bundle, int n, hisq_prec prec,
+                               void* const dst[], void* stream);
 
 /*
  * Even-odd normal operator of M = 2m + D at mu = 0:
@@ -326,7 +366,10 @@ typedef struct {
     int check_every;       /* host convergence poll interval (10) */
     int use_graphs;        /* 1: replay iterations from a captured CUDA graph (1) */
     int rhs_per_thread;    /* Dslash rhs per thread: 0 = auto, else 1/2/4/8 */
-    hisq_layout spinor_layout; /* layout of the CG's internal vectors (HISQ_AOS) */
+    hisq_layout spinor_layout; /* layout of the CG's internal low-precision vectors
+                                  (HISQ_BUNDLE; where n is not a multiple of the
+                                  chunk width, or for F64 and full-lattice solves,
+                                  the solve uses HISQ_AOS) */
 } hisq_cg_params;
 
 typedef struct {

@@ -40,7 +40,11 @@ FAMILIES = [
     ("dslash_f16_12_14", dict(HISQ_STORE="__half", HISQ_LSTORE="hisq::Fx16", HISQ_RU=12, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
     ("dslash_f16_14_14", dict(HISQ_STORE="__half", HISQ_LSTORE="hisq::Fx16", HISQ_RU=14, HISQ_RN=14, HISQ_MAX_RPT=8, HISQ_WITH_XY=0)),
 ]
-PLAIN = ["hisq_api", "dslash_dispatch", "gauge", "blas", "force", "noalloc"]
+PLAIN = ["hisq_api", "dslash_dispatch", "gauge", "blas", "blas_bundle", "force", "noalloc"]
+# bundle-layout Dslash families (FP32 / FP16 storage); the U r18 / N r14 ones
+# carry every mapping the autotuner chooses from
+BUNDLE_FAMILIES = [(name, defs, 1 if (defs["HISQ_RU"], defs["HISQ_RN"]) == (18, 14) else 0)
+                   for name, defs in FAMILIES if defs["HISQ_STORE"] != "double"]
 
 
 def _nvcc() -> str:
@@ -91,6 +95,14 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
             dflags += [f"-DHISQ_FAMILY={name}_{suffix}", f"-DHISQ_LAYOUT={layout}"]
             tasks.append(([nvcc, *ARCH, *NVFLAGS, *dflags, "-c", os.path.join(CSRC, "dslash_inst.cu"),
                            "-o", obj], obj))
+    for name, defs, full in BUNDLE_FAMILIES:
+        obj = os.path.join(BUILD, f"{name}_bundle.o")
+        dflags = [f"-D{k}={v}" for k, v in defs.items() if k in ("HISQ_STORE", "HISQ_LSTORE", "HISQ_RU", "HISQ_RN")]
+        dflags += [f"-DHISQ_FAMILY={name}_bundle", f"-DHISQ_BUNDLE_FULL={full}"]
+        tasks.append(([nvcc, *ARCH, *NVFLAGS, *dflags, "-c", os.path.join(CSRC, "dslash_bundle_inst.cu"),
+                       "-o", obj], obj))
+    # longest compiles first
+    tasks.sort(key=lambda t: 0 if "_bundle.o" in t[1] else 1)
     jobs = jobs or min(len(tasks), max(1, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(_compile, tasks))

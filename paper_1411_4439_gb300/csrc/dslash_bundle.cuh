@@ -1,0 +1,364 @@
+// Multi-rhs Dslash on the rhs-interleaved bundle layout (Eq. 3 on a bundle,
+// Eq. 4), the kernel of the mixed-precision CG.
+//
+// Bundle layout: 16-byte chunks, each holding one colour of W consecutive rhs
+// at one site, real parts first:
+//   FP32 storage (W = 2): float4  (re_k, re_k+1, im_k, im_k+1)
+//   FP16 storage (W = 4): 8 halves (re_k .. re_k+3, im_k .. im_k+3)
+// Chunk (group g = k / W, colour c, site h) is element (3 g + c) V_h + h of
+// the buffer. A warp of 32 consecutive sites reads 512 contiguous bytes per
+// chunk row, for the neighbours of every hop (the y, z, t hops shift the row
+// by a constant; the x hops stay inside it).
+//
+// Thread mapping: one output site and R rhs per thread (R / W chunks per
+// colour), blockDim.y groups of R rhs sharing the sites of a block. Per hop
+// the thread loads one link (reconstructed in registers) and 3 R / W chunks.
+//
+// Arithmetic: with PK the rhs are processed in pairs by packed FP32
+// instructions (fma.rn.f32x2): for a link element m = (mr, mi) and the pair
+// vectors VR = (re_k, re_k+1), VI = (im_k, im_k+1)
+//   forward  acc += m v      : AR += (mr,mr) VR + (-mi,-mi) VI ; AI += (mr,mr) VI + (mi,mi) VR
+//   backward acc -= m^dag v  : AR += (-mr,-mr) VR + (-mi,-mi) VI ; AI += (-mr,-mr) VI + (mi,mi) VR
+// so one link element serves R / 2 pairs with 3 packed operands. Without PK
+// every rhs takes scalar FMAs. Accumulation is FP32 in both.
+//
+// Pipelining: the link of hop e + LD and the neighbour chunks of hop e + SD
+// (LD, SD in {0, 1}) are loaded before hop e is multiplied.
+#pragma once
+
+#include "dslash_impl.cuh"
+
+namespace hisq {
+
+template <typename S> struct Bundle;
+template <> struct Bundle<float> {
+    static constexpr int W = 2;
+};
+template <> struct Bundle<__half> {
+    static constexpr int W = 4;
+};
+
+// Pair j of a chunk as packed (re, re') and (im, im').
+__device__ __forceinline__ void chunk_pair(const uint4& c, int j, f2x& vr, f2x& vi, float) {
+    // FP32: one pair per chunk
+    vr = pk2(__uint_as_float(c.x), __uint_as_float(c.y));
+    vi = pk2(__uint_as_float(c.z), __uint_as_float(c.w));
+}
+__device__ __forceinline__ float2 h2f(unsigned u) {
+    __half2 h;
+    memcpy(&h, &u, 4);
+    return __half22float2(h);
+}
+__device__ __forceinline__ void chunk_pair(const uint4& c, int j, f2x& vr, f2x& vi, __half) {
+    const float2 r = h2f(j ? c.y : c.x);
+    const float2 i = h2f(j ? c.w : c.z);
+    vr = pk2(r.x, r.y);
+    vi = pk2(i.x, i.y);
+}
+
+// rhs l of a chunk as a complex number (scalar arithmetic path).
+__device__ __forceinline__ float2 chunk_rhs(const uint4& c, int l, float) {
+    return l == 0 ? make_float2(__uint_as_float(c.x), __uint_as_float(c.z))
+                  : make_float2(__uint_as_float(c.y), __uint_as_float(c.w));
+}
+__device__ __forceinline__ float2 chunk_rhs(const uint4& c, int l, __half) {
+    const float2 r = h2f(l < 2 ? c.x : c.y);
+    const float2 i = h2f(l < 2 ? c.z : c.w);
+    return (l & 1) ? make_float2(r.y, i.y) : make_float2(r.x, i.x);
+}
+
+// Chunk holding rhs values w[0 .. W) of one colour.
+__device__ __forceinline__ uint4 make_chunk(const float2 (&w)[2], float) {
+    return make_uint4(__float_as_uint(w[0].x), __float_as_uint(w[1].x), __float_as_uint(w[0].y),
+                      __float_as_uint(w[1].y));
+}
+__device__ __forceinline__ unsigned f2h(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    unsigned u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+__device__ __forceinline__ uint4 make_chunk(const float2 (&w)[4], __half) {
+    return make_uint4(f2h(w[0].x, w[1].x), f2h(w[2].x, w[3].x), f2h(w[0].y, w[1].y), f2h(w[2].y, w[3].y));
+}
+// The values a chunk store leaves in memory (FP16 rounds).
+__device__ __forceinline__ float2 stored_rhs(float2 v, float) { return v; }
+__device__ __forceinline__ float2 stored_rhs(float2 v, __half) {
+    return __half22float2(__floats2half2_rn(v.x, v.y));
+}
+
+template <typename S, typename LS, int RU, int RN, int R, bool PK, int LD, int SD>
+struct BundleHops {
+    using LC = typename Traits<LS>::C;
+    static constexpr int W = Bundle<S>::W;
+    static constexpr int NG = R / W;   // chunks per colour
+    static constexpr int P = R / 2;    // rhs pairs
+    static constexpr int NCU = (RU == 18) ? 9 : (RU == 14 ? 7 : 6);
+    static constexpr int NCN = (RN == 18) ? 9 : (RN == 14 ? 7 : 6);
+    static constexpr int NCMAX = NCU > NCN ? NCU : NCN;
+    static_assert(R % W == 0 && R % 2 == 0, "rhs per thread must fill whole chunks and pairs");
+
+    struct Raw {
+        LC l[NCMAX];
+        uint4 v[3][NG];
+    };
+
+    const DslashArgs& a;
+    const LC* __restrict__ Ub;
+    const LC* __restrict__ Nb;
+    const uint4* __restrict__ in;   // this thread's first chunk row: group k0 / W
+    int vh, p, q, h, hrow, x, y, z, t;
+    f2x (&ar)[P][3];
+    f2x (&ai)[P][3];
+    float2 (&acc)[R][3];
+
+    __device__ __forceinline__ BundleHops(const DslashArgs& args, int h_, int k0, f2x (&ar_)[P][3],
+                                          f2x (&ai_)[P][3], float2 (&acc_)[R][3])
+        : a(args), ar(ar_), ai(ai_), acc(acc_) {
+        Ub = reinterpret_cast<const LC*>(a.U);
+        Nb = reinterpret_cast<const LC*>(a.N);
+        vh = a.g.vh;
+        in = reinterpret_cast<const uint4*>(a.in[0]) + (size_t)(k0 / W) * 3 * vh;
+        p = a.parity;
+        q = 1 - p;
+        h = h_;
+        const int xh = h % a.g.hx;
+        int r = h / a.g.hx;
+        y = r % a.g.L[1];
+        r /= a.g.L[1];
+        z = r % a.g.L[2];
+        t = r / a.g.L[2];
+        x = 2 * xh + ((p + y + z + t) & 1);
+        hrow = h - xh;
+    }
+
+    template <int MU>
+    __device__ __forceinline__ int coord() const {
+        return MU == 0 ? x : MU == 1 ? y : MU == 2 ? z : t;
+    }
+
+    template <int E>
+    __device__ __forceinline__ int neighbour() const {
+        constexpr int MU = E >> 2, HOP = E & 3;
+        constexpr int D = HOP == 0 ? 1 : HOP == 1 ? -1 : HOP == 2 ? 3 : -3;
+        const int c = coord<MU>();
+        const int cn = wrap(c + D, a.g.L[MU]);
+        if (MU == 0) return hrow + (cn >> 1);
+        const int stride = MU == 1 ? a.g.sy : MU == 2 ? a.g.sz : a.g.st;
+        return h + (cn - c) * stride;
+    }
+
+    template <int E>
+    __device__ __forceinline__ void issue_link(Raw& b) const {
+        constexpr int MU = E >> 2, HOP = E & 3;
+        constexpr bool NAIK = HOP >= 2;
+        constexpr bool BACK = HOP & 1;
+        constexpr int NC = NAIK ? NCN : NCU;
+        const LC* base = (NAIK ? Nb : Ub) + (size_t)((BACK ? q : p) * 4 + MU) * NC * vh;
+        const int li = BACK ? neighbour<E>() : h;
+        load_link_raw<LC, NC>(b.l, base, vh, li);
+    }
+
+    template <int E>
+    __device__ __forceinline__ void issue_spin(Raw& b) const {
+        const int hn = neighbour<E>();
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int g = 0; g < NG; ++g) b.v[c][g] = __ldg(in + (size_t)(g * 3 + c) * vh + hn);
+    }
+
+    template <int E>
+    __device__ __forceinline__ void compute(const Raw& b) {
+        constexpr int MU = E >> 2, HOP = E & 3;
+        constexpr bool NAIK = HOP >= 2;
+        constexpr bool BACK = HOP & 1;
+        constexpr int REC = NAIK ? RN : RU;
+        constexpr int NC = NAIK ? NCN : NCU;
+        const float* sc = NAIK ? a.lscale_n : a.lscale_u;
+        Link<float2> m;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
+        if constexpr (REC == 18) {
+#pragma unroll
+            for (int c = 6; c < 9; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
+        } else if constexpr (REC == 14) {
+            third_row(m, link_elem(b.l[NC - 1], sc[NC - 1]));
+        } else {
+            const int e = MU == 0 ? 0 : MU == 1 ? x : MU == 2 ? (x + y) : (x + y + z);
+            int sgn = (e & 1) ? -1 : 1;
+            if (MU == 3 && ((HOP == 0 && t == a.g.L[3] - 1) || (HOP == 1 && t == 0))) sgn = -sgn;
+            const float inv_s = (float)a.r12_inv_scale;
+            third_row(m, make_float2(sgn > 0 ? inv_s : -inv_s, 0.f));
+        }
+        if (MU == 3 && a.has_mu) {
+            const double f = HOP == 0 ? a.ft1 : HOP == 1 ? a.bt1 : HOP == 2 ? a.ft3 : a.bt3;
+            scale_link(m, (float)f);
+        }
+        if constexpr (PK) {
+            f2x vr[P][3], vi[P][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp)
+                    chunk_pair(b.v[j][(2 * pp) / W], ((2 * pp) % W) / 2, vr[pp][j], vi[pp][j], S{});
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float2 e = BACK ? m.e[3 * j + i] : m.e[3 * i + j];
+                    const f2x A = BACK ? pk2(-e.x, -e.x) : pk2(e.x, e.x);
+                    const f2x B = pk2(-e.y, -e.y);
+                    const f2x C = pk2(e.y, e.y);
+#pragma unroll
+                    for (int pp = 0; pp < P; ++pp) {
+                        ar[pp][i] = fma2(A, vr[pp][j], ar[pp][i]);
+                        ar[pp][i] = fma2(B, vi[pp][j], ar[pp][i]);
+                        ai[pp][i] = fma2(A, vi[pp][j], ai[pp][i]);
+                        ai[pp][i] = fma2(C, vr[pp][j], ai[pp][i]);
+                    }
+                }
+        } else {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                float2 v[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] = chunk_rhs(b.v[c][k / W], k % W, S{});
+                if (BACK)
+                    mv_sub_dag(acc[k], m, v);
+                else
+                    mv_add(acc[k], m, v);
+            }
+        }
+    }
+
+    template <int E>
+    __device__ __forceinline__ void step(Raw (&buf)[2]) {
+        if constexpr (E + LD < 16) issue_link<E + LD>(buf[(E + LD) & 1]);
+        if constexpr (E + SD < 16) issue_spin<E + SD>(buf[(E + SD) & 1]);
+        compute<E>(buf[E & 1]);
+        if constexpr (E + 1 < 16) step<E + 1>(buf);
+    }
+
+    __device__ __forceinline__ void run() {
+        Raw buf[2];
+        if constexpr (LD == 1) issue_link<0>(buf[0]);
+        if constexpr (SD == 1) issue_spin<0>(buf[0]);
+        step<0>(buf);
+    }
+};
+
+// One Dslash of parity a.parity on the bundle layout: out = D in (EPI_NONE)
+// or out = cx x + cd (D in) with optionally Re<x, out> per rhs (EPI_X), for
+// the rhs of every thread group. a.in[0], a.out[0], a.x[0] are bundle bases.
+template <typename S, typename LS, int RU, int RN, int R, int MINB, bool PK, int LD, int SD, int EPI>
+__global__ void __launch_bounds__(128, MINB) dslash_bundle_kernel(const DslashArgs a) {
+    constexpr int W = Bundle<S>::W;
+    constexpr int NG = R / W;
+    constexpr int P = R / 2;
+    const int vh = a.g.vh;
+    const int k0 = threadIdx.y * R;
+    const size_t gofs = (size_t)(k0 / W) * 3 * vh;
+
+    float red0[R], red1[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        red0[j] = 0.f;
+        red1[j] = 0.f;
+    }
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h - (int)threadIdx.x < vh;
+         h += gridDim.x * blockDim.x) {
+        if (h >= vh) continue;
+        if constexpr (EPI == EPI_X) {
+            // the epilogue's x is read after the hops; start it towards L2 now
+            const uint4* xb = reinterpret_cast<const uint4*>(a.x[0]) + gofs + h;
+#pragma unroll
+            for (int c = 0; c < 3 * NG; ++c)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(xb + (size_t)c * vh));
+        }
+        f2x ar[P][3], ai[P][3];
+        float2 acc[R][3];
+#pragma unroll
+        for (int pp = 0; pp < P; ++pp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ar[pp][c] = 0ull;
+                ai[pp][c] = 0ull;
+            }
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[k][c] = make_float2(0.f, 0.f);
+        {
+            BundleHops<S, LS, RU, RN, R, PK, LD, SD> hops(a, h, k0, ar, ai, acc);
+            hops.run();
+        }
+        if constexpr (PK) {
+#pragma unroll
+            for (int pp = 0; pp < P; ++pp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 re = up2(ar[pp][c]), im = up2(ai[pp][c]);
+                    acc[2 * pp][c] = make_float2(re.x, im.x);
+                    acc[2 * pp + 1][c] = make_float2(re.y, im.y);
+                }
+        }
+        // epilogue: out = [cx x +] cd acc, stored as chunks
+        const float cx = (float)a.cx, cd = (float)a.cd;
+        const uint4* xb = EPI == EPI_X ? reinterpret_cast<const uint4*>(a.x[0]) + gofs + h : nullptr;
+        uint4* ob = reinterpret_cast<uint4*>(a.out[0]) + gofs + h;
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float2 w[W];
+                if constexpr (EPI == EPI_X) {
+                    const uint4 xc = __ldg(xb + (size_t)(g * 3 + c) * vh);
+#pragma unroll
+                    for (int l = 0; l < W; ++l) {
+                        const float2 xv = chunk_rhs(xc, l, S{});
+                        const float2 av = acc[g * W + l][c];
+                        w[l] = make_float2(fmaf(cd, av.x, cx * xv.x), fmaf(cd, av.y, cx * xv.y));
+                        if (a.red_mode == RED_DOT_XW) {
+                            const float2 sv = stored_rhs(w[l], S{});
+                            red0[g * W + l] = fmaf(xv.x, sv.x, fmaf(xv.y, sv.y, red0[g * W + l]));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int l = 0; l < W; ++l) w[l] = acc[g * W + l][c];
+                }
+                ob[(size_t)(g * 3 + c) * vh] = make_chunk(w, S{});
+            }
+    }
+    if (a.red_mode == RED_NONE) return;
+    block_reduce_finish<R>(a, k0, red0, red1);
+}
+
+// Whether (n, rhs per thread) fits the bundle kernel of storage S.
+template <typename S>
+__host__ __device__ constexpr bool bundle_shape_ok(int n, int rpt) {
+    return rpt % Bundle<S>::W == 0 && rpt % 2 == 0 && n % rpt == 0 && n / rpt >= 1 && n / rpt <= 4;
+}
+
+template <typename S, typename LS, int RU, int RN, int R, int MINB, bool PK, int LD, int SD, int EPI>
+cudaError_t launch_dslash_bundle(const DslashArgs& a, cudaStream_t s) {
+    if (a.t_only || !bundle_shape_ok<S>(a.nrhs, R)) return cudaErrorInvalidValue;
+    if (EPI == EPI_NONE && a.red_mode != RED_NONE) return cudaErrorInvalidValue;
+    const int G = a.nrhs / R;
+    if (G > 4) return cudaErrorInvalidValue;
+    const int bx = 128 / G;   // 128 threads: 128 / G sites x G rhs groups
+    const dim3 block(bx, G);
+    auto* kern = dslash_bundle_kernel<S, LS, RU, RN, R, MINB, PK, LD, SD, EPI>;
+    int occ = 0;
+    cudaError_t e = cached_occupancy(kern, bx * G, 0, 0, &occ);
+    if (e != cudaSuccess) return e;
+    long long nblk = ((long long)a.g.vh + bx - 1) / bx;
+    const long long cap = (long long)occ * device_sm_count();
+    if (nblk > cap) nblk = cap;
+    if (nblk > kMaxRedBlocks) nblk = kMaxRedBlocks;
+    kern<<<(unsigned)nblk, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace hisq

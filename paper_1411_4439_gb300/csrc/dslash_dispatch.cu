@@ -24,7 +24,55 @@ HISQ_FAMILY_DECL(dslash_f16_12_14);
 HISQ_FAMILY_DECL(dslash_f16_14_14);
 #undef HISQ_FAMILY_DECL
 
+// bundle-layout families (dslash_bundle_inst.cu)
+cudaError_t dslash_f32_18_18_bundle(const DslashArgs&, int, int, int, int, cudaStream_t);
+cudaError_t dslash_f32_18_14_bundle(const DslashArgs&, int, int, int, int, cudaStream_t);
+cudaError_t dslash_f32_12_14_bundle(const DslashArgs&, int, int, int, int, cudaStream_t);
+cudaError_t dslash_f32_14_14_bundle(const DslashArgs&, int, int, int, int, cudaStream_t);
+cudaError_t dslash_f16_18_18_bundle(const DslashArgs&, int, int, int, int, cudaStream_t);
+cudaError_t dslash_f16_18_14_bundle(const DslashArgs&, int, int, int, int, cudaStream_t);
+cudaError_t dslash_f16_12_14_bundle(const DslashArgs&, int, int, int, int, cudaStream_t);
+cudaError_t dslash_f16_14_14_bundle(const DslashArgs&, int, int, int, int, cudaStream_t);
+
 int dslash_max_rpt(int prec) { return prec == HISQ_F64 ? 4 : 8; }
+
+// (rpt, minb, kind) keys of the bundle kernels: every family has the default
+// mappings; the U r18 / N r14 families (the configurations' compression) also
+// the variants the autotuner chooses from.
+bool bundle_mapping_built(int prec, int ru, int rn, int rpt, int minb, int kind) {
+    if (prec != HISQ_F32 && prec != HISQ_F16) return false;
+    const int key = rpt * 100 + minb * 10 + kind;
+    if (key == 825 || key == 435) return true;
+    if (!(ru == 18 && rn == 14)) return false;
+    switch (key) {
+        case 815: case 835: case 445: case 816: case 826: case 436: case 827: case 837: case 437:
+        case 447: case 828: case 838: case 448:
+            return true;
+        default:
+            return false;
+    }
+}
+
+// Default bundle mapping for n rhs: eight rhs per thread when n allows
+// (every link element then serves four rhs pairs), else four.
+DslashTune dslash_bundle_tune(int prec, int n) {
+    DslashTune t;
+    t.layout = HISQ_BUNDLE;
+    t.kind = KIND_BUNDLE;
+    t.prefetch = 0;
+    t.rpt = 0;
+    t.minb = 0;
+    const int W = bundle_width(prec);
+    if (W == 0 || n % W != 0) return t;
+    if (n % 8 == 0 && n / 8 <= 4) {
+        t.rpt = 8;
+        t.minb = 2;
+    } else if (n % 4 == 0 && n / 4 <= 4) {
+        t.rpt = 4;
+        t.minb = 3;
+    }
+    return t;
+}
 
 // (rpt, minb, kind) triples compiled in dslash_inst.cu
 bool dslash_mapping_built(int prec, int rpt, int minb, int kind) {
@@ -88,9 +136,34 @@ bool dslash_variant_supported(int prec, int ru, int rn, int epi) {
            (ru == 14 && rn == 14);
 }
 
+static cudaError_t launch_bundle(const DslashArgs& a, int prec, int ru, int rn, int epi,
+                                 const DslashTune& t, cudaStream_t s) {
+    if (!bundle_mapping_built(prec, ru, rn, t.rpt, t.minb, t.kind)) return cudaErrorInvalidValue;
+    if (epi != EPI_NONE && epi != EPI_X) return cudaErrorInvalidValue;
+    const int r = t.rpt, b = t.minb, k = t.kind;
+    const int key = ru * 100 + rn;
+    if (prec == HISQ_F32) {
+        switch (key) {
+            case 1818: return dslash_f32_18_18_bundle(a, epi, r, b, k, s);
+            case 1814: return dslash_f32_18_14_bundle(a, epi, r, b, k, s);
+            case 1214: return dslash_f32_12_14_bundle(a, epi, r, b, k, s);
+            case 1414: return dslash_f32_14_14_bundle(a, epi, r, b, k, s);
+        }
+    } else if (prec == HISQ_F16) {
+        switch (key) {
+            case 1818: return dslash_f16_18_18_bundle(a, epi, r, b, k, s);
+            case 1814: return dslash_f16_18_14_bundle(a, epi, r, b, k, s);
+            case 1214: return dslash_f16_12_14_bundle(a, epi, r, b, k, s);
+            case 1414: return dslash_f16_14_14_bundle(a, epi, r, b, k, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_dslash(const DslashArgs& a, int prec, int ru, int rn, int epi,
                           const DslashTune& t, cudaStream_t s) {
     if (!dslash_variant_supported(prec, ru, rn, epi)) return cudaErrorInvalidValue;
+    if (t.layout == HISQ_BUNDLE) return launch_bundle(a, prec, ru, rn, epi, t, s);
     if (!dslash_mapping_built(prec, t.rpt, t.minb, t.kind)) return cudaErrorInvalidValue;
     if (a.t_only && (t.kind == KIND_PIPE1 || t.kind == KIND_PIPE2)) {
         // the pipelined kernels run all 16 hops; temporal-only operators take

@@ -10,6 +10,8 @@
 // per-rhs reductions the CG needs (Re<x,out> or |out|^2 and max|out_i|).
 #pragma once
 
+#include <atomic>
+
 #include "hisq_internal.cuh"
 #include "reduce.cuh"
 
@@ -525,6 +527,32 @@ __device__ __forceinline__ void block_reduce_finish(const DslashArgs& a, int k0,
     }
 }
 
+// Resident blocks per SM of a kernel, cached per device (the first call on a
+// device measures it; every later call reads it).
+// The first call on a device also sets the kernel's shared-memory attribute
+// there: the whole SRAM as L1 when smem == 0 (the kernels gather their
+// neighbour vectors through L1), else the dynamic shared memory size.
+template <typename K>
+cudaError_t cached_occupancy(K* kern, int threads, size_t smem, int slot, int* occ) {
+    static std::atomic<int> cache[64][16];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || slot < 0 || slot >= 16) return cudaErrorInvalidValue;
+    int v = cache[dev][slot].load(std::memory_order_relaxed);
+    if (v == 0) {
+        e = smem == 0 ? cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0)
+                      : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        if (v < 1) v = 1;
+        cache[dev][slot].store(v, std::memory_order_relaxed);
+    }
+    *occ = v;
+    return cudaSuccess;
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launcher for one instance
 // ---------------------------------------------------------------------------
@@ -536,18 +564,9 @@ cudaError_t launch_dslash_instance(const DslashArgs& a, cudaStream_t s) {
     bx &= ~31;
     const dim3 block(bx, G);
     auto* kern = dslash_kernel<S, LS, RU, RN, RPT, MINB, EPI, LAYOUT, PACK>;
-    static int occ_cache[9] = {0};
-    int occ = occ_cache[G];
-    if (occ == 0) {
-        // the kernel uses almost no shared memory: give the SM's SRAM to L1,
-        // which catches the neighbour gathers
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bx * G, 0);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-        occ_cache[G] = occ;
-    }
+    int occ = 0;
+    cudaError_t e = cached_occupancy(kern, bx * G, 0, G, &occ);
+    if (e != cudaSuccess) return e;
     long long nblk = ((long long)a.g.vh + bx - 1) / bx;
     long long cap = (long long)occ * device_sm_count();
     if (nblk > cap) nblk = cap;

@@ -253,16 +253,9 @@ cudaError_t launch_dslash_pipe(const DslashArgs& a, cudaStream_t s) {
     bx &= ~31;
     const dim3 block(bx, G);
     auto* kern = dslash_pipe_kernel<S, LS, RU, RN, RPT, MINB, DEPTH, EPI, LAYOUT>;
-    static int occ_cache[9] = {0};
-    int occ = occ_cache[G];
-    if (occ == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bx * G, 0);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-        occ_cache[G] = occ;
-    }
+    int occ = 0;
+    cudaError_t e = cached_occupancy(kern, bx * G, 0, G, &occ);
+    if (e != cudaSuccess) return e;
     long long nblk = ((long long)a.g.vh + bx - 1) / bx;
     long long cap = (long long)occ * device_sm_count();
     if (nblk > cap) nblk = cap;

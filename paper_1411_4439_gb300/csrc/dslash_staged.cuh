@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(staged_max_threads(RPT), MINB) dslash_staged_k
     const int first = blockIdx.x;
     int step = 0;
     bool ok = true;
+    bool next_issued = false;   // the copies of step + 1 were issued during step
     if (tid == 0 && first < ntiles)
         issue_direction<LC, NCU, NCN>(bufs, Ub, Nb, g, p, first * TS, 0, &bars[0]);
 
@@ -254,9 +255,10 @@ __global__ void __launch_bounds__(staged_max_threads(RPT), MINB) dslash_staged_k
             const int b = step & 1;
             // the buffer of the next step was last read in the previous step
             __syncthreads();
+            const int ntile = (mu == 3) ? tile + gridDim.x : tile;
+            next_issued = ntile < ntiles;
             if (tid == 0) {
                 const int nmu = (mu + 1) & 3;
-                const int ntile = (mu == 3) ? tile + gridDim.x : tile;
                 if (ntile < ntiles) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     issue_direction<LC, NCU, NCN>(bufs + (size_t)(b ^ 1) * NSTAGE * TS, Ub, Nb, g, p,
@@ -324,10 +326,13 @@ __global__ void __launch_bounds__(staged_max_threads(RPT), MINB) dslash_staged_k
         epilogue_site<SC, RPT, EPI, LAYOUT>(a, h, k0, acc, red0, red1);
     }
     if (!ok) {
-        // record the failure, then give the copies this block may still have
-        // in flight a bounded chance to land before the block exits
+        // Record the failure. No bulk copy may still be writing into this
+        // block's shared memory when it exits, so both buffers' outstanding
+        // copies get a bounded chance to land: those of the step whose wait
+        // gave up, and those of the next step if they were issued.
         if (tid == 0 && a.status != nullptr) atomicOr(a.status, kFlagTimeout);
-        mbar_wait_bounded(&bars[(step + 1) & 1], ((step + 1) >> 1) & 1);
+        mbar_wait_bounded(&bars[step & 1], (step >> 1) & 1);
+        if (next_issued) mbar_wait_bounded(&bars[(step + 1) & 1], ((step + 1) >> 1) & 1);
         return;
     }
     if (a.red_mode == RED_NONE) return;
@@ -356,16 +361,9 @@ cudaError_t launch_dslash_staged(const DslashArgs& a, cudaStream_t s) {
     const dim3 block(kStagedTile, G);
     const size_t smem = 2ull * 2 * (NCU + NCN) * kStagedTile * sizeof(LC);
     auto* kern = dslash_staged_kernel<S, LS, RU, RN, RPT, MINB, EPI, LAYOUT>;
-    static int occ_cache[3] = {0};
-    int occ = occ_cache[G];
-    if (occ == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStagedTile * G, smem);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-        occ_cache[G] = occ;
-    }
+    int occ = 0;
+    cudaError_t e = cached_occupancy(kern, kStagedTile * G, smem, G, &occ);
+    if (e != cudaSuccess) return e;
     long long nblk = a.g.vh / kStagedTile;
     const long long cap = (long long)occ * device_sm_count();
     if (nblk > cap) nblk = cap;

@@ -10,6 +10,7 @@
 // fell by `reliable_delta`, or when an iterated residual claims
 // convergence), and replays the iterations from a captured CUDA graph.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -95,16 +96,20 @@ namespace hisq {
 void record_error(const char* msg) { g_last_error = msg; }
 
 int device_sm_count() {
-    static int cached[64] = {0};
+    // per device; atomic so that host threads launching concurrently read
+    // either 0 (and query) or the stored count
+    static std::atomic<int> cached[64];
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    if (cached[dev] == 0) {
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
         int n = 0;
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = n > 0 ? n : 1;
+        v = n > 0 ? n : 1;
+        cached[dev].store(v, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return v;
 }
 }  // namespace hisq
 
@@ -362,10 +367,11 @@ extern "C" hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rpt, int minb, 
         return fail(HISQ_EINVAL, "rhs per thread must be 0 (auto), 1, 2, 4 or 8");
     if (minb < 0 || minb > 8) return fail(HISQ_EINVAL, "min blocks per SM must be 0 (auto) .. 8");
     if (flags & ~(HISQ_MAP_PACKED | HISQ_MAP_L2_PREFETCH | HISQ_MAP_STAGED | HISQ_MAP_PIPELINED |
-                  HISQ_MAP_PIPELINED2))
+                  HISQ_MAP_PIPELINED2 | HISQ_MAP_SCALAR | HISQ_MAP_NO_LOOKAHEAD))
         return fail(HISQ_EINVAL, "unknown mapping flags %d", flags);
     const int kinds = !!(flags & HISQ_MAP_PACKED) + !!(flags & HISQ_MAP_STAGED) +
-                      !!(flags & HISQ_MAP_PIPELINED) + !!(flags & HISQ_MAP_PIPELINED2);
+                      !!(flags & HISQ_MAP_PIPELINED) + !!(flags & HISQ_MAP_PIPELINED2) +
+                      !!(flags & HISQ_MAP_SCALAR) + !!(flags & HISQ_MAP_NO_LOOKAHEAD);
     if (kinds > 1) return fail(HISQ_EINVAL, "mapping flags %d name more than one kernel kind", flags);
     g->tune_rpt = rpt;
     g->tune_minb = minb;
@@ -441,6 +447,9 @@ extern "C" hisq_status hisq_link_reconstruct(const int L[4], const void* packed,
 // ---------------------------------------------------------------------------
 namespace {
 
+int link_recon_u(hisq_gauge g, int prec) { return prec == HISQ_F64 ? 18 : g->recon_U; }
+int link_recon_n(hisq_gauge g, int prec) { return prec == HISQ_F64 ? 18 : g->recon_N; }
+
 int auto_rpt(int n, int prec) {
     const int mx = dslash_max_rpt(prec);
     int r = 1;
@@ -462,7 +471,19 @@ int kind_of_flags(int flags) {
     return KIND_REG;
 }
 
+int bundle_kind_of_flags(int flags) {
+    if (flags & HISQ_MAP_SCALAR) return KIND_BUNDLE_SCALAR;
+    if (flags & HISQ_MAP_NO_LOOKAHEAD) return KIND_BUNDLE_NOLA;
+    if (flags & (HISQ_MAP_PIPELINED | HISQ_MAP_PIPELINED2)) return KIND_BUNDLE_SPIN;
+    return KIND_BUNDLE;
+}
+
 int flags_of_tune(const DslashTune& t) {
+    if (t.layout == HISQ_BUNDLE)
+        return t.kind == KIND_BUNDLE_SCALAR ? HISQ_MAP_SCALAR
+               : t.kind == KIND_BUNDLE_NOLA ? HISQ_MAP_NO_LOOKAHEAD
+               : t.kind == KIND_BUNDLE_SPIN ? HISQ_MAP_PIPELINED
+                                            : 0;
     const int k = t.kind == KIND_PACKED   ? HISQ_MAP_PACKED
                   : t.kind == KIND_STAGED ? HISQ_MAP_STAGED
                   : t.kind == KIND_PIPE1  ? HISQ_MAP_PIPELINED
@@ -475,6 +496,30 @@ int flags_of_tune(const DslashTune& t) {
 // setting, else the autotuned mapping for (n, prec, layout), else the
 // largest power of two dividing n (at most 8 rhs groups per block).
 DslashTune pick_tune(hisq_gauge g, int n, int prec, int requested, int layout) {
+    if (layout == HISQ_BUNDLE) {
+        // the bundle kernel (rpt 0 when n does not fit the layout)
+        if (!requested && g->tune_rpt == 0 && g->tune_flags == 0) {
+            auto it = g->tuned.find(tuned_key(n, prec, layout));
+            if (it != g->tuned.end()) return it->second;
+        }
+        DslashTune t = dslash_bundle_tune(prec, n);
+        if (t.rpt == 0) return t;
+        const int ru = link_recon_u(g, prec), rn = link_recon_n(g, prec);
+        const int r = requested ? requested : g->tune_rpt;
+        if (r && n % r == 0 && n / r <= 4) {
+            const int b = (!requested && g->tune_minb) ? g->tune_minb : (r == 8 ? 2 : 3);
+            const int k = requested ? KIND_BUNDLE : bundle_kind_of_flags(g->tune_flags);
+            if (bundle_mapping_built(prec, ru, rn, r, b, k)) {
+                t.rpt = r;
+                t.minb = b;
+                t.kind = k;
+            }
+        } else if (!requested && g->tune_flags) {
+            const int k = bundle_kind_of_flags(g->tune_flags);
+            if (bundle_mapping_built(prec, ru, rn, t.rpt, t.minb, k)) t.kind = k;
+        }
+        return t;
+    }
     if (!requested && g->tune_rpt == 0 && g->tune_flags == 0) {
         auto it = g->tuned.find(tuned_key(n, prec, layout));
         if (it != g->tuned.end()) return it->second;
@@ -494,16 +539,24 @@ DslashTune pick_tune(hisq_gauge g, int n, int prec, int requested, int layout) {
 
 }  // namespace
 
-extern "C" hisq_status hisq_get_dslash_mapping(hisq_gauge g, int n, hisq_prec prec, int* rpt, int* minb,
-                                              int* flags) {
+extern "C" hisq_status hisq_get_dslash_mapping_ex(hisq_gauge g, int n, hisq_prec prec, hisq_layout layout,
+                                                 int* rpt, int* minb, int* flags) {
     if (!g) return fail(HISQ_EINVAL, "NULL handle");
     if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
     if (!valid_prec(prec)) return fail(HISQ_EINVAL, "unknown precision %d", prec);
-    const DslashTune t = pick_tune(g, n, prec, 0, HISQ_AOS);
+    if (layout != HISQ_AOS && layout != HISQ_SOA && layout != HISQ_BUNDLE)
+        return fail(HISQ_EINVAL, "unknown layout %d", layout);
+    const DslashTune t = pick_tune(g, n, prec, 0, layout);
+    if (layout == HISQ_BUNDLE && t.rpt == 0) return fail(HISQ_EINVAL, "no bundle kernel for n = %d", n);
     if (rpt) *rpt = t.rpt;
     if (minb) *minb = t.minb;
     if (flags) *flags = flags_of_tune(t);
     return HISQ_OK;
+}
+
+extern "C" hisq_status hisq_get_dslash_mapping(hisq_gauge g, int n, hisq_prec prec, int* rpt, int* minb,
+                                              int* flags) {
+    return hisq_get_dslash_mapping_ex(g, n, prec, HISQ_AOS, rpt, minb, flags);
 }
 
 namespace {
@@ -540,9 +593,6 @@ void set_mu(DslashArgs& a, double mu) {
     a.has_mu = (mu != 0.0) ? 1 : 0;
 }
 
-int link_recon_u(hisq_gauge g, int prec) { return prec == HISQ_F64 ? 18 : g->recon_U; }
-int link_recon_n(hisq_gauge g, int prec) { return prec == HISQ_F64 ? 18 : g->recon_N; }
-
 hisq_status check_spinors(hisq_gauge g, const void* const v[], void* const w[], int n, int prec) {
     if (!g) return fail(HISQ_EINVAL, "NULL handle");
     if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
@@ -560,19 +610,51 @@ hisq_status check_spinors(hisq_gauge g, const void* const v[], void* const w[], 
     return HISQ_OK;
 }
 
+// Bundle buffers: n fits the chunk width of prec, one 16-byte-aligned pointer each.
+hisq_status check_bundle(hisq_gauge g, const void* v, const void* w, int n, int prec) {
+    if (!g) return fail(HISQ_EINVAL, "NULL handle");
+    const int W = bundle_width(prec);
+    if (W == 0) return fail(HISQ_EINVAL, "the bundle layout needs F32 or F16 storage");
+    if (prec != g->prec)
+        return fail(HISQ_EINVAL, "spinor precision %d needs links stored in the same precision (handle has %d)",
+                    prec, g->prec);
+    if (n < W || n > kMaxRhs || n % W != 0)
+        return fail(HISQ_EINVAL, "n = %d: the bundle layout of this precision needs a multiple of %d up to %d", n,
+                    W, kMaxRhs);
+    if (!v || !w) return fail(HISQ_EINVAL, "NULL bundle pointer");
+    if ((uintptr_t)v % 16 || (uintptr_t)w % 16) return fail(HISQ_EINVAL, "bundle pointers must be 16-byte aligned");
+    return HISQ_OK;
+}
+
 }  // namespace
 
 extern "C" hisq_status hisq_dslash_ex(hisq_gauge g, double mu, const void* const v[], void* const w[],
                                       int n, int parity, hisq_prec spinor_prec, hisq_layout layout,
                                       void* stream) {
-    hisq_status st = check_spinors(g, v, w, n, spinor_prec);
-    if (st != HISQ_OK) return st;
+    if (layout == HISQ_BUNDLE) {
+        if (!v || !w) return fail(HISQ_EINVAL, "NULL pointer array");
+        hisq_status st = check_bundle(g, v[0], w[0], n, spinor_prec);
+        if (st != HISQ_OK) return st;
+    } else {
+        hisq_status st = check_spinors(g, v, w, n, spinor_prec);
+        if (st != HISQ_OK) return st;
+    }
     if (parity != 0 && parity != 1) return fail(HISQ_EINVAL, "parity must be 0 or 1");
-    if (layout != HISQ_AOS && layout != HISQ_SOA) return fail(HISQ_EINVAL, "unknown layout %d", layout);
+    if (layout != HISQ_AOS && layout != HISQ_SOA && layout != HISQ_BUNDLE)
+        return fail(HISQ_EINVAL, "unknown layout %d", layout);
     if (!std::isfinite(mu)) return fail(HISQ_EINVAL, "mu must be finite");
     DslashArgs a;
     fill_common(a, g, spinor_prec, parity, n);
     set_mu(a, mu);
+    if (layout == HISQ_BUNDLE) {
+        a.in[0] = v[0];
+        a.out[0] = w[0];
+        const DslashTune t = pick_tune(g, n, spinor_prec, 0, layout);
+        if (t.rpt == 0) return fail(HISQ_EINVAL, "no bundle kernel for n = %d", n);
+        HISQ_CUDA(launch_dslash(a, spinor_prec, link_recon_u(g, spinor_prec), link_recon_n(g, spinor_prec),
+                                EPI_NONE, t, (cudaStream_t)stream));
+        return HISQ_OK;
+    }
     for (int k = 0; k < n; ++k) {
         a.in[k] = v[k];
         a.out[k] = w[k];
@@ -586,6 +668,37 @@ extern "C" hisq_status hisq_dslash_ex(hisq_gauge g, double mu, const void* const
 extern "C" hisq_status hisq_dslash(hisq_gauge g, const void* const v[], void* const w[], int n,
                                    int parity, hisq_prec spinor_prec, void* stream) {
     return hisq_dslash_ex(g, 0.0, v, w, n, parity, spinor_prec, HISQ_AOS, stream);
+}
+
+extern "C" hisq_status hisq_bundle_pack(hisq_gauge g, const void* const src[], int n, hisq_prec prec,
+                                        void* bundle, void* stream) {
+    hisq_status st = check_bundle(g, bundle, bundle, n, prec);
+    if (st != HISQ_OK) return st;
+    if (!src) return fail(HISQ_EINVAL, "NULL pointer array");
+    BundlePtrs p;
+    memset(&p, 0, sizeof(p));
+    for (int k = 0; k < n; ++k) {
+        if (!src[k] || (uintptr_t)src[k] % 16) return fail(HISQ_EINVAL, "source %d is NULL or not 16-byte aligned", k);
+        p.p[k] = (const double2*)src[k];
+    }
+    HISQ_CUDA(launch_bundle_pack(p, n, prec, g->g.vh, bundle, (cudaStream_t)stream));
+    return HISQ_OK;
+}
+
+extern "C" hisq_status hisq_bundle_unpack(hisq_gauge g, const void* bundle, int n, hisq_prec prec,
+                                          void* const dst[], void* stream) {
+    hisq_status st = check_bundle(g, bundle, bundle, n, prec);
+    if (st != HISQ_OK) return st;
+    if (!dst) return fail(HISQ_EINVAL, "NULL pointer array");
+    BundlePtrs p;
+    memset(&p, 0, sizeof(p));
+    for (int k = 0; k < n; ++k) {
+        if (!dst[k] || (uintptr_t)dst[k] % 16)
+            return fail(HISQ_EINVAL, "destination %d is NULL or not 16-byte aligned", k);
+        p.p[k] = (const double2*)dst[k];
+    }
+    HISQ_CUDA(launch_bundle_unpack(bundle, p, n, prec, g->g.vh, (cudaStream_t)stream));
+    return HISQ_OK;
 }
 
 extern "C" hisq_status hisq_mdagm(hisq_gauge g, double mass, const void* const v[], void* const w[],
@@ -633,6 +746,24 @@ namespace {
 
 std::vector<DslashTune> candidate_tunes(hisq_gauge g, int n, int prec, int layout) {
     std::vector<DslashTune> out;
+    if (layout == HISQ_BUNDLE) {
+        const int ru = link_recon_u(g, prec), rn = link_recon_n(g, prec);
+        const int kinds[] = {KIND_BUNDLE, KIND_BUNDLE_SPIN, KIND_BUNDLE_SCALAR, KIND_BUNDLE_NOLA};
+        for (int r : {4, 8}) {
+            if (n % r != 0 || n / r > 4) continue;
+            for (int b = 1; b <= 4; ++b)
+                for (int k : kinds) {
+                    if (!bundle_mapping_built(prec, ru, rn, r, b, k)) continue;
+                    DslashTune t = dslash_bundle_tune(prec, n);
+                    if (t.rpt == 0) continue;
+                    t.rpt = r;
+                    t.minb = b;
+                    t.kind = k;
+                    out.push_back(t);
+                }
+        }
+        return out;
+    }
     const int rpts[] = {1, 2, 4, 8};
     const int minbs[] = {1, 2, 3, 4};
     const int kinds[] = {KIND_REG, KIND_PACKED, KIND_STAGED, KIND_PIPE1, KIND_PIPE2};
@@ -659,7 +790,10 @@ extern "C" hisq_status hisq_autotune_dslash(hisq_gauge g, int n, hisq_prec prec,
     if (n < 1 || n > kMaxRhs) return fail(HISQ_EINVAL, "n = %d outside 1..%d", n, kMaxRhs);
     if (!valid_prec(prec) || (prec != HISQ_F64 && prec != g->prec))
         return fail(HISQ_EINVAL, "precision %d not available on this handle", prec);
-    if (layout != HISQ_AOS && layout != HISQ_SOA) return fail(HISQ_EINVAL, "unknown layout %d", layout);
+    if (layout != HISQ_AOS && layout != HISQ_SOA && layout != HISQ_BUNDLE)
+        return fail(HISQ_EINVAL, "unknown layout %d", layout);
+    if (layout == HISQ_BUNDLE && dslash_bundle_tune(prec, n).rpt == 0)
+        return fail(HISQ_EINVAL, "no bundle kernel for n = %d in precision %d", n, prec);
     if (reps < 1) reps = 5;
     std::lock_guard<std::mutex> lock(g->mtx);
     const size_t per = (size_t)g->g.vh * 3 * prec_complex_bytes(prec);
@@ -687,9 +821,11 @@ extern "C" hisq_status hisq_autotune_dslash(hisq_gauge g, int n, hisq_prec prec,
         a.in[k] = (char*)buf + per * k;
         a.out[k] = (char*)buf + per * (n + k);
     }
+    if (layout == HISQ_BUNDLE) a.out[0] = (char*)buf + per * n;   // one bundle in, one out
     const int ru = link_recon_u(g, prec), rn = link_recon_n(g, prec);
     double best = HUGE_VAL;
-    DslashTune best_t = dslash_default_tune(prec, auto_rpt(n, prec), layout);
+    DslashTune best_t = layout == HISQ_BUNDLE ? dslash_bundle_tune(prec, n)
+                                              : dslash_default_tune(prec, auto_rpt(n, prec), layout);
     for (const DslashTune& t : candidate_tunes(g, n, prec, layout)) {
         e = launch_dslash(a, prec, ru, rn, EPI_NONE, t, s);   // warm-up (and first-use set-up)
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
@@ -769,18 +905,24 @@ extern "C" hisq_status hisq_gauge_load_tuned(const int L[4], const void* U, cons
             last = st;
             break;
         }
-        double sec_soa = 0.0, sec_aos = 0.0;
+        // the layout the CG runs on (the bundle where n fits it) decides; the
+        // ABI layouts are tuned too for direct Dslash calls
+        const bool bundle = prec != HISQ_F64 && dslash_bundle_tune(prec, n).rpt != 0;
+        double sec_cg = 0.0, sec_soa = 0.0, sec_aos = 0.0;
         st = hisq_autotune_dslash(g, n, prec, HISQ_SOA, 5, nullptr, nullptr, nullptr, &sec_soa);
         if (st == HISQ_OK) st = hisq_autotune_dslash(g, n, prec, HISQ_AOS, 5, nullptr, nullptr, nullptr, &sec_aos);
+        if (st == HISQ_OK && bundle)
+            st = hisq_autotune_dslash(g, n, prec, HISQ_BUNDLE, 5, nullptr, nullptr, nullptr, &sec_cg);
+        if (!bundle) sec_cg = sec_aos;
         if (st != HISQ_OK) {
             hisq_gauge_free(g);
             last = st;
             break;
         }
-        if (sec_soa < best_s) {
+        if (sec_cg < best_s) {
             if (best) hisq_gauge_free(best);
             best = g;
-            best_s = sec_soa;
+            best_s = sec_cg;
         } else {
             hisq_gauge_free(g);
         }
@@ -807,6 +949,7 @@ extern "C" hisq_status hisq_autotune_bundle(hisq_gauge g, int n_max, hisq_prec p
     int bn = 0;
     double bs = HUGE_VAL;
     for (int n = 1; n <= n_max; n *= 2) {
+        if (layout == HISQ_BUNDLE && dslash_bundle_tune(prec, n).rpt == 0) continue;   // n does not fill a chunk
         double sec = 0.0;
         hisq_status st = hisq_autotune_dslash(g, n, prec, layout, reps, nullptr, nullptr, nullptr, &sec);
         if (st != HISQ_OK) return st;
@@ -942,7 +1085,8 @@ extern "C" void hisq_cg_default_params(hisq_cg_params* p) {
     p->check_every = 10;
     p->use_graphs = 1;
     p->rhs_per_thread = 0;
-    p->spinor_layout = HISQ_AOS;   // the ABI layout: no transposes, and the early-x epilogue fits in registers
+    // the bundle layout where n fits it (F32 / F16 even-odd solves), else AoS
+    p->spinor_layout = HISQ_BUNDLE;
 }
 
 namespace {
@@ -1008,6 +1152,7 @@ struct Solver {
     hisq_gauge g;
     Workspace* w;
     int n, prec, full;
+    bool bundle = false;       // low-precision vectors in the bundle layout
     DslashTune tune, tune64;   // inner (low precision) and FP64 Dslash mappings
     double mass, mu;
     double tol2;
@@ -1051,6 +1196,22 @@ struct Solver {
     cudaError_t apply_lo(cudaStream_t s) const {
         const int ru = g->recon_U, rn = g->recon_N;
         cudaError_t e;
+        if (bundle) {
+            DslashArgs a = args(1, prec);   // t = D_oe p
+            a.in[0] = w->p_lo;
+            a.out[0] = w->t_lo;
+            e = launch_dslash(a, prec, ru, rn, EPI_NONE, tune, s);
+            if (e != cudaSuccess) return e;
+            DslashArgs b = args(0, prec);   // Ap = 4m^2 p - D_eo t, pAp = Re<p, Ap>
+            b.cx = 4.0 * mass * mass;
+            b.cd = -1.0;
+            b.red_mode = RED_DOT_XW;
+            b.finish = FIN_CG_ALPHA;
+            b.in[0] = w->t_lo;
+            b.out[0] = w->Ap_lo;
+            b.x[0] = w->p_lo;
+            return launch_dslash(b, prec, ru, rn, EPI_X, tune, s);
+        }
         if (!full) {
             DslashArgs a = args(1, prec);   // t = D_oe p
             for (int k = 0; k < n; ++k) {
@@ -1105,6 +1266,11 @@ struct Solver {
     // One CG iteration on every active rhs.
     cudaError_t iterate(cudaStream_t s) const {
         cudaError_t e = apply_lo(s);
+        if (bundle) {
+            if (e == cudaSuccess) e = launch_cg_update_r_bundle(blas(), prec, w->r_lo, w->Ap_lo, s);
+            if (e == cudaSuccess) e = launch_cg_update_px_bundle(blas(), prec, w->x_lo, w->r_lo, w->p_lo, s);
+            return e;
+        }
         if (e == cudaSuccess) e = launch_cg_update_r(blas(), prec, w->r_lo, w->Ap_lo, s);
         if (e == cudaSuccess) e = launch_cg_update_px(blas(), prec, w->x_lo, w->r_lo, w->p_lo, s);
         return e;
@@ -1166,10 +1332,20 @@ struct Solver {
         return launch_residual_norm(blas(), w->r_hi, tol2, s);
     }
 
+    cudaError_t accum(cudaStream_t s) const {
+        return bundle ? launch_accum_solution_bundle(blas(), prec, w->x_hi, w->x_lo, g->g.vh, s)
+                      : launch_accum_solution(blas(), prec, w->x_hi, w->x_lo, s);
+    }
+
+    cudaError_t rescale(int reset_p, cudaStream_t s) const {
+        return bundle ? launch_reliable_rescale_bundle(blas(), prec, w->r_hi, w->r_lo, w->p_lo, reset_p, g->g.vh, s)
+                      : launch_reliable_rescale(blas(), prec, w->r_hi, w->r_lo, w->p_lo, reset_p, s);
+    }
+
     cudaError_t reliable_update(cudaStream_t s) const {
-        cudaError_t e = launch_accum_solution(blas(), prec, w->x_hi, w->x_lo, s);
+        cudaError_t e = accum(s);
         if (e == cudaSuccess) e = true_residual(s);
-        if (e == cudaSuccess) e = launch_reliable_rescale(blas(), prec, w->r_hi, w->r_lo, w->p_lo, 0, s);
+        if (e == cudaSuccess) e = rescale(0, s);
         return e;
     }
 
@@ -1262,7 +1438,7 @@ struct CgRun {
         if (prm.maxiter < 1) return fail(HISQ_EINVAL, "maxiter must be >= 1");
         if (prm.check_every < 1) prm.check_every = 1;
         if (prm.reliable_every < 1) prm.reliable_every = 1 << 30;
-        if (prm.spinor_layout != HISQ_AOS && prm.spinor_layout != HISQ_SOA)
+        if (prm.spinor_layout != HISQ_AOS && prm.spinor_layout != HISQ_SOA && prm.spinor_layout != HISQ_BUNDLE)
             return fail(HISQ_EINVAL, "unknown spinor layout %d", prm.spinor_layout);
         if (!(prm.reliable_delta >= 0.0 && prm.reliable_delta < 1.0))
             return fail(HISQ_EINVAL, "reliable_delta must be in [0, 1)");
@@ -1285,8 +1461,14 @@ struct CgRun {
         sv.n = n;
         sv.prec = prm.inner_prec;
         sv.full = full;
+        // the bundle layout where it fits, else the ABI layout
+        if (prm.spinor_layout == HISQ_BUNDLE) {
+            const DslashTune tb = full ? DslashTune{} : pick_tune(g, n, sv.prec, prm.rhs_per_thread, HISQ_BUNDLE);
+            sv.bundle = !full && bundle_width(sv.prec) != 0 && tb.rpt != 0;
+            if (!sv.bundle) prm.spinor_layout = HISQ_AOS;
+        }
         sv.tune = pick_tune(g, n, sv.prec, prm.rhs_per_thread, prm.spinor_layout);
-        sv.tune64 = pick_tune(g, n, HISQ_F64, 0, prm.spinor_layout);
+        sv.tune64 = pick_tune(g, n, HISQ_F64, 0, sv.bundle ? HISQ_AOS : prm.spinor_layout);
         sv.mass = mass;
         sv.mu = mu;
         sv.tol2 = tol * tol;
@@ -1317,7 +1499,7 @@ struct CgRun {
         } else {
             HISQ_CUDA(launch_copy_residual(sv.blas(), w->b_hi, w->r_hi, sv.tol2, s));
         }
-        HISQ_CUDA(launch_reliable_rescale(sv.blas(), sv.prec, w->r_hi, w->r_lo, w->p_lo, 1, s));
+        HISQ_CUDA(sv.rescale(1, s));
         HISQ_CUDA(sv.poll(s));
         update_stop();
         return HISQ_OK;
@@ -1405,7 +1587,7 @@ struct CgRun {
         }
         if (w->cg_host->flags) {
             // fold what the low-precision solution gathered so far into x
-            HISQ_CUDA(launch_accum_solution(sv.blas(), sv.prec, w->x_hi, w->x_lo, s));
+            HISQ_CUDA(sv.accum(s));
             HISQ_CUDA(sv.poll(s));
         }
         const CgScalars& h = *w->cg_host;

@@ -226,12 +226,18 @@ enum Epi : int { EPI_NONE = 0, EPI_X = 1, EPI_XY = 2 };
 // the register kernel, 1 the register kernel with packed f32x2 complex
 // arithmetic (FP32 arithmetic only), 2 the kernel with links staged in shared
 // memory by bulk copies (FP32 arithmetic only).
-enum DslashKind : int { KIND_REG = 0, KIND_PACKED = 1, KIND_STAGED = 2, KIND_PIPE1 = 3, KIND_PIPE2 = 4 };
+// Kinds 5 to 8 run on the bundle spinor layout (dslash_bundle.cuh): packed
+// f32x2 arithmetic with the next hop's link in flight (5), also the next
+// hop's neighbours in flight (6), scalar arithmetic (7), no look-ahead (8).
+enum DslashKind : int {
+    KIND_REG = 0, KIND_PACKED = 1, KIND_STAGED = 2, KIND_PIPE1 = 3, KIND_PIPE2 = 4,
+    KIND_BUNDLE = 5, KIND_BUNDLE_SPIN = 6, KIND_BUNDLE_SCALAR = 7, KIND_BUNDLE_NOLA = 8
+};
 struct DslashTune {
     int rpt;
     int minb;
     int kind;
-    int layout;     // HISQ_AOS or HISQ_SOA
+    int layout;     // HISQ_AOS, HISQ_SOA or HISQ_BUNDLE
     int prefetch;   // bulk L2 prefetch of each tile's links
 };
 
@@ -248,6 +254,13 @@ DslashTune dslash_register_tune(int prec, int rpt, int layout);
 bool dslash_staged_ok(const Geom& g, int prec, int rpt, int groups);
 // Largest rhs-per-thread value instantiated for a precision.
 int dslash_max_rpt(int prec);
+// Bundle layout: rhs per 16-byte chunk of a storage precision (F32: 2,
+// F16: 4; 0 where there is no bundle kernel), whether a bundle mapping is
+// built for a link compression pair, and the default bundle mapping for n
+// rhs (rpt 0 when n does not fit the layout).
+int bundle_width(int prec);
+bool bundle_mapping_built(int prec, int ru, int rn, int rpt, int minb, int kind);
+DslashTune dslash_bundle_tune(int prec, int n);
 
 // Spinor layout conversion of FP64 vectors: n rhs, `halves` parity blocks of
 // vh sites each; to_soa: [h][V_h][3] -> [h][3][V_h], else the reverse.
@@ -312,6 +325,25 @@ cudaError_t launch_copy_residual(const BlasArgs& a, const double2* b, double2* r
 // rr = rr_rel = |r_lo|^2 (active rhs only)
 cudaError_t launch_reliable_rescale(const BlasArgs& a, int prec, const double2* r_hi,
                                     void* r_lo, void* p_lo, int reset_p, cudaStream_t s);
+
+// Bundle-layout versions (blas_bundle.cu): vectors [n / W][3][V_h] chunks of
+// 16 bytes (W rhs each); a.len = 3 V_h; x_lo is FP32 [n / W][3][V_h] chunks of
+// W complex numbers (real parts, then imaginary parts).
+cudaError_t launch_cg_update_r_bundle(const BlasArgs& a, int prec, void* r, const void* Ap, cudaStream_t s);
+cudaError_t launch_cg_update_px_bundle(const BlasArgs& a, int prec, void* x, const void* r, void* p,
+                                       cudaStream_t s);
+cudaError_t launch_accum_solution_bundle(const BlasArgs& a, int prec, double2* x_hi, void* x_lo, int vh,
+                                         cudaStream_t s);
+cudaError_t launch_reliable_rescale_bundle(const BlasArgs& a, int prec, const double2* r_hi, void* r_lo,
+                                           void* p_lo, int reset_p, int vh, cudaStream_t s);
+struct BundlePtrs {
+    const double2* p[kMaxRhs];
+};
+// n FP64 [V_h][3] vectors <-> one bundle of storage prec (pack rounds to it).
+cudaError_t launch_bundle_pack(const BundlePtrs& ptrs, int n, int prec, long long vh, void* bundle,
+                               cudaStream_t s);
+cudaError_t launch_bundle_unpack(const void* bundle, const BundlePtrs& ptrs, int n, int prec, long long vh,
+                                 cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Gradients (force.cu)

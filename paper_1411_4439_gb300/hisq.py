@@ -27,7 +27,7 @@ HISQ_EBREAKDOWN, HISQ_ENAN, HISQ_ECUDA, HISQ_ETIMEOUT, HISQ_ENOMEM = 4, 5, 6, 7,
 # precisions and compressions
 HISQ_F64, HISQ_F32, HISQ_F16 = 0, 1, 2
 HISQ_R18, HISQ_R12, HISQ_R14 = 18, 12, 14
-HISQ_AOS, HISQ_SOA = 0, 1
+HISQ_AOS, HISQ_SOA, HISQ_BUNDLE = 0, 1, 2
 
 STATUS_NAMES = {0: "HISQ_OK", 1: "HISQ_EINVAL", 2: "HISQ_ERECON", 3: "HISQ_ENOCONV",
                 4: "HISQ_EBREAKDOWN", 5: "HISQ_ENAN", 6: "HISQ_ECUDA", 7: "HISQ_ETIMEOUT",
@@ -38,12 +38,15 @@ HISQ_OP_M, HISQ_OP_MDAG, HISQ_OP_DM_DMU = 0, 1, 2
 HISQ_OP_D2M_DMU2, HISQ_OP_D3M_DMU3, HISQ_OP_D4M_DMU4 = 3, 4, 5
 HISQ_MAP_PACKED, HISQ_MAP_L2_PREFETCH, HISQ_MAP_STAGED = 1, 2, 4
 HISQ_MAP_PIPELINED, HISQ_MAP_PIPELINED2 = 8, 16
+HISQ_MAP_SCALAR, HISQ_MAP_NO_LOOKAHEAD = 32, 64
 
 EXPORTED = ["hisq_version", "hisq_last_error", "hisq_gauge_load", "hisq_gauge_free",
             "hisq_gauge_info", "hisq_set_dslash_mapping", "hisq_get_dslash_mapping",
+            "hisq_get_dslash_mapping_ex",
             "hisq_autotune_dslash", "hisq_gauge_load_tuned", "hisq_autotune_bundle",
             "hisq_link_compress",
-            "hisq_link_reconstruct", "hisq_dslash", "hisq_dslash_ex", "hisq_mdagm",
+            "hisq_link_reconstruct", "hisq_dslash", "hisq_dslash_ex", "hisq_bundle_pack",
+            "hisq_bundle_unpack", "hisq_mdagm",
             "hisq_apply_m", "hisq_link_force", "hisq_cdot", "hisq_cdot_noalloc",
             "hisq_cg_default_params", "hisq_cg_solve", "hisq_cg_solve_batched"]
 
@@ -97,6 +100,7 @@ def library() -> ctypes.CDLL:
         "hisq_gauge_info": (c_int, [vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_size_t)]),
         "hisq_set_dslash_mapping": (c_int, [vp, c_int, c_int, c_int]),
         "hisq_get_dslash_mapping": (c_int, [vp, c_int, c_int, ip, ip, ip]),
+        "hisq_get_dslash_mapping_ex": (c_int, [vp, c_int, c_int, c_int, ip, ip, ip]),
         "hisq_autotune_dslash": (c_int, [vp, c_int, c_int, c_int, c_int, ip, ip, ip,
                                          ctypes.POINTER(c_double)]),
         "hisq_gauge_load_tuned": (c_int, [ip, vp, vp, c_int, c_int, c_int, c_double, vp, ctypes.POINTER(vp)]),
@@ -107,6 +111,8 @@ def library() -> ctypes.CDLL:
         "hisq_dslash_ex": (c_int, [vp, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int,
                                    c_int, c_int, vp]),
         "hisq_mdagm": (c_int, [vp, c_double, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_int, vp]),
+        "hisq_bundle_pack": (c_int, [vp, ctypes.POINTER(vp), c_int, c_int, vp, vp]),
+        "hisq_bundle_unpack": (c_int, [vp, vp, c_int, c_int, ctypes.POINTER(vp), vp]),
         "hisq_apply_m": (c_int, [vp, c_double, c_double, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                  c_int, c_int, vp]),
         "hisq_link_force": (c_int, [vp, c_double, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int,
@@ -288,6 +294,14 @@ def hisq_get_dslash_mapping(g: Gauge, n: int, prec: int) -> tuple:
     return r.value, b.value, f.value
 
 
+def hisq_get_dslash_mapping_ex(g: Gauge, n: int, prec: int, layout: int) -> tuple:
+    """(rhs per thread, min blocks, HISQ_MAP_* flags) a Dslash of n rhs in `layout` will use."""
+    r, b, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(library().hisq_get_dslash_mapping_ex(g.handle, int(n), int(prec), int(layout), ctypes.byref(r),
+                                                ctypes.byref(b), ctypes.byref(f)))
+    return r.value, b.value, f.value
+
+
 def hisq_autotune_dslash(g: Gauge, n: int, prec: int, layout: int = HISQ_SOA, reps: int = 5) -> dict:
     """Time every built Dslash mapping for (n, prec, layout), keep the fastest on g."""
     r, b, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
@@ -325,12 +339,68 @@ def hisq_dslash(g: Gauge, v, w, parity: int, prec: int, stream=None) -> None:
 
 
 def hisq_dslash_ex(g: Gauge, mu: float, v, w, parity: int, prec: int, layout: int = HISQ_AOS,
-                   stream=None) -> None:
-    """Dslash with a chemical potential on the temporal hops; AoS or SoA spinors."""
+                   stream=None, n: int | None = None) -> None:
+    """Dslash with a chemical potential on the temporal hops.
+
+    AoS or SoA: v, w lists of one device tensor per rhs. HISQ_BUNDLE: v, w are
+    single device tensors holding the bundle of all ``n`` rhs.
+    """
+    if layout == HISQ_BUNDLE:
+        if n is None:
+            raise ValueError("the bundle layout needs n")
+        _check_bundle_tensor(v, prec, n, g)
+        _check_bundle_tensor(w, prec, n, g)
+        _check(library().hisq_dslash_ex(g.handle, float(mu), _ptr_array([v]), _ptr_array([w]), int(n),
+                                        int(parity), int(prec), int(layout), _stream_handle(stream, v)))
+        return
     if len(v) != len(w):
         raise ValueError("v and w need the same number of rhs")
     _check(library().hisq_dslash_ex(g.handle, float(mu), _ptr_array(v), _ptr_array(w), len(v),
                                     int(parity), int(prec), int(layout), _stream_handle(stream, *v)))
+
+
+def bundle_bytes(g: Gauge, n: int, prec: int) -> int:
+    """Bytes of a bundle of n rhs on one parity of g's lattice."""
+    vh = int(np.prod(g.L)) // 2
+    return n * 3 * vh * (8 if prec == HISQ_F32 else 4)
+
+
+def _check_bundle_tensor(t, prec: int, n: int, g: Gauge):
+    if not _is_device(t):
+        raise ValueError("bundle buffers must be CUDA tensors")
+    if t.numel() * t.element_size() != bundle_bytes(g, n, prec):
+        raise ValueError(f"bundle buffer has {t.numel() * t.element_size()} bytes, "
+                         f"{bundle_bytes(g, n, prec)} expected for n = {n}")
+
+
+def hisq_bundle_pack(g: Gauge, src, prec: int, bundle, stream=None) -> None:
+    """Pack FP64 complex vectors src[k] ([V_h][3], device) into one bundle of prec."""
+    _check_fp64_vectors(src)
+    _check_bundle_tensor(bundle, prec, len(src), g)
+    _check(library().hisq_bundle_pack(g.handle, _ptr_array(src), len(src), int(prec), _ptr(bundle),
+                                      _stream_handle(stream, bundle)))
+
+
+def hisq_bundle_unpack(g: Gauge, bundle, prec: int, dst, stream=None) -> None:
+    """Unpack one bundle of prec into FP64 complex vectors dst[k] ([V_h][3], device)."""
+    _check_fp64_vectors(dst)
+    _check_bundle_tensor(bundle, prec, len(dst), g)
+    _check(library().hisq_bundle_unpack(g.handle, _ptr(bundle), len(dst), int(prec), _ptr_array(dst),
+                                        _stream_handle(stream, bundle)))
+
+
+def _check_fp64_vectors(vs):
+    """Every vector a CUDA complex128 (or float64 pairs) tensor of one device and length."""
+    torch = _torch()
+    if len(vs) == 0:
+        raise ValueError("no vectors")
+    for t in vs:
+        if not hasattr(t, "is_cuda") or not t.is_cuda:
+            raise ValueError("vectors must be CUDA tensors")
+        if t.dtype not in (torch.complex128, torch.float64):
+            raise ValueError(f"vectors must be complex128 or float64, got {t.dtype}")
+        if t.dtype != vs[0].dtype or t.device != vs[0].device or t.numel() != vs[0].numel():
+            raise ValueError("vectors must share dtype, device and length")
 
 
 def hisq_mdagm(g: Gauge, mass: float, v, w, prec: int, stream=None) -> None:
@@ -362,10 +432,8 @@ def hisq_cdot(g: Gauge, a, b, stream=None) -> np.ndarray:
     if len(a) != len(b):
         raise ValueError("a and b need the same number of rhs")
     n = len(a)
+    _check_fp64_vectors(list(a) + list(b))
     length = int(a[0].numel()) // (2 if str(a[0].dtype).endswith("float64") else 1)
-    for t in list(a) + list(b):
-        if t.numel() != a[0].numel():
-            raise ValueError("all vectors need the same length")
     out = (ctypes.c_double * (2 * n))()
     _check(library().hisq_cdot(g.handle, _ptr_array(a), _ptr_array(b), n, length, out,
                                _stream_handle(stream, *a)))
@@ -378,10 +446,8 @@ def hisq_cdot_noalloc(a, b, stream=None) -> np.ndarray:
     if len(a) != len(b):
         raise ValueError("a and b need the same number of rhs")
     n = len(a)
+    _check_fp64_vectors(list(a) + list(b))
     length = int(a[0].numel()) // (2 if str(a[0].dtype).endswith("float64") else 1)
-    for t in list(a) + list(b):
-        if t.numel() != a[0].numel():
-            raise ValueError("all vectors need the same length")
     out = (ctypes.c_double * (2 * max(n, 1)))()
     _check(library().hisq_cdot_noalloc(_ptr_array(a), _ptr_array(b), n, length, out,
                                        _stream_handle(stream, *a)))

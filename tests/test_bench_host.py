@@ -75,11 +75,21 @@ def test_reference_arm_is_silent_on_other_ranks(monkeypatch, capsys):
     assert capsys.readouterr().out == ""
 
 
-def test_roofline_traffic_only_for_the_captured_mapping():
-    name, traffic = bench.dslash_kernel_name(4, 2, 16, (32, 32, 32, 8))
-    assert "dslash_pipe_kernel" in name and "depth=2" in name and traffic > 0
-    assert bench.dslash_kernel_name(8, 2, 0, (32, 32, 32, 8))[1] is None
-    assert bench.dslash_kernel_name(4, 2, 16, (48, 48, 48, 12))[1] is None
+def test_fp32_peak_and_roofline_bound():
+    # 152 SMs x 128 lanes x 2 flop x 2070 MHz
+    assert bench.fp32_peak_tflops(152, 2070.0) == pytest.approx(80.548, abs=1e-3)
+    peak, hbm = bench.fp32_peak_tflops(152, 2070.0), 6777.0
+    vh = 663552
+    f16 = (bench.DSLASH_FLOPS_PER_SITE_RHS * 8 * vh, bench.dslash_bytes_per_site(8, 18, 14, 2, 2) * vh)
+    f32 = (bench.DSLASH_FLOPS_PER_SITE_RHS * 8 * vh, bench.dslash_bytes_per_site(8, 18, 14, 4, 4) * vh)
+    assert bench.roofline_bound(*f16, peak, hbm) == "alu"     # 13.0 flop/B past the ridge of 11.9
+    assert bench.roofline_bound(*f32, peak, hbm) == "hbm"     # 6.5 flop/B
+
+
+def test_roofline_traffic_only_for_a_captured_configuration():
+    assert bench.dslash_traffic("f16", (48, 48, 48, 12), 8, (3, 3, 3)) is None
+    for key, value in bench.DSLASH_TRAFFIC.items():
+        assert bench.dslash_traffic(key[0], key[1], key[2], key[3:]) == value > 0
 
 
 def test_warmup_is_clamped_to_three():
