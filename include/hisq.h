@@ -158,15 +158,16 @@ enum {
     HISQ_MAP_STAGED = 4,
     HISQ_MAP_PIPELINED = 8,
     HISQ_MAP_PIPELINED2 = 16,
-    HISQ_MAP_SCALAR = 32,
-    HISQ_MAP_NO_LOOKAHEAD = 64
+    HISQ_MAP_COMPACT = 128
 };
 /* On the bundle layout (rhs per thread 4 or 8, min blocks per SM of 128-thread
  * blocks 1..4) the kernel multiplies rhs pairs with packed FP32 (f32x2)
  * instructions and keeps the next hop's link load in flight; flags select
  * variants: HISQ_MAP_PIPELINED also the next hop's neighbour chunks,
- * HISQ_MAP_SCALAR scalar FP32 arithmetic, HISQ_MAP_NO_LOOKAHEAD no loads
- * ahead of the current hop. */
+ * HISQ_MAP_COMPACT a hop loop with the direction as a runtime loop (a quarter
+ * of the code, one colour of the neighbours converted at a time),
+ * HISQ_MAP_STAGED the neighbour chunks copied into shared memory by
+ * asynchronous per-thread copies one hop ahead (two with HISQ_MAP_PIPELINED2). */
 hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_blocks,
                                     int flags);
 
@@ -275,7 +276,9 @@ hisq_status hisq_bundle_unpack(hisq_gauge g, const void* bundle, int n, hisq_pre
                                void* const dst[], void* stream);
 
 /*
- * Even-odd normal operator of M = 2m + D at mu = 0:
+ * Even-odd normal operator of M = 2m + D at mu = 0 (Sec. 1: the fermion
+ * matrix is inverted; its hopping part is the Dslash of Eq. 3, which only
+ * couples opposite parities, so M^dag M splits into parity blocks):
  *   w[k] = A_e v[k] = 4 m^2 v[k] - D_eo D_oe v[k]   (even sites)
  * A_e = (M^dag M) restricted to even sites, Hermitian positive definite.
  * v, w as for hisq_dslash with parity 0. Uses a cached odd-parity temporary on
@@ -310,7 +313,9 @@ hisq_status hisq_apply_m(hisq_gauge g, double mass, double mu, int op,
                          hisq_prec spinor_prec, void* stream);
 
 /*
- * Link force for gradients of a solve. For FP64 parity-blocked vectors a_k,
+ * Link force for gradients of a solve (derivatives of the stochastic trace
+ * estimators of Eq. 2, Sec. 1, with respect to the links of Eq. 3). For
+ * FP64 parity-blocked vectors a_k,
  * b_k ([2][V_h][3] complex128, device) accumulates into `out` (device,
  * complex128 [4][V][3][3], canonical link layout)
  *   out[mu][x] += coef * sum_k [ f a_k(x) b_k(x+hop mu)^dag
@@ -324,6 +329,7 @@ hisq_status hisq_link_force(hisq_gauge g, double mu, int hop, const void* const 
                             void* stream);
 
 /*
+ * The bilinears eta^dag X eta of Eq. 2 (Sec. 1), per rhs:
  * out[2k] + i out[2k+1] = <a_k, b_k> = sum_i conj(a_k[i]) b_k[i] over `len`
  * complex128 numbers, in FP64 with a fixed summation order. a, b: n device
  * pointers; out: host array of 2n doubles. Uses reduction scratch owned by
@@ -383,7 +389,11 @@ typedef struct {
 void hisq_cg_default_params(hisq_cg_params* p);
 
 /*
- * Conjugate gradient on the normal equations of M = 2m + D, n independent
+ * The inversion of the fermion matrix for many random vectors at once
+ * (abstract; Sec. 1: the vectors of a bundle share each Dslash of Eq. 4;
+ * Sec. 3: the CG with several rhs). Independent coefficients per vector
+ * (no block Krylov space) are this library's reading. Conjugate gradient on the normal
+ * equations of M = 2m + D, n independent
  * CGs (one per rhs, own alpha and beta) sharing every Dslash. Stops rhs k
  * when ||b_k - A x_k|| / ||b_k|| <= tol in FP64 (tol > 0). p may be NULL
  * (defaults); stats may be NULL.
@@ -408,7 +418,9 @@ hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu,
                           hisq_cg_stats* stats, void* stream);
 
 /*
- * Several independent solves advanced together, e.g. bundles on gauge fields
+ * Several independent solves advanced together (Sec. 3, Fig. 4 right: the
+ * inverter for a fixed number of rhs on lattices of different size), e.g.
+ * bundles on gauge fields
  * of uneven volume: each chunk of iterations of all unfinished solves is one
  * CUDA graph whose branches run the solves concurrently, so small lattices
  * share the GPU instead of running one after another. Every problem has its

@@ -210,13 +210,16 @@ struct BundleHops {
                     const f2x A = BACK ? pk2(-e.x, -e.x) : pk2(e.x, e.x);
                     const f2x B = pk2(-e.y, -e.y);
                     const f2x C = pk2(e.y, e.y);
+                    // four passes over the pairs, so that an accumulator's
+                    // next update is 2 P instructions after its last one
 #pragma unroll
-                    for (int pp = 0; pp < P; ++pp) {
-                        ar[pp][i] = fma2(A, vr[pp][j], ar[pp][i]);
-                        ar[pp][i] = fma2(B, vi[pp][j], ar[pp][i]);
-                        ai[pp][i] = fma2(A, vi[pp][j], ai[pp][i]);
-                        ai[pp][i] = fma2(C, vr[pp][j], ai[pp][i]);
-                    }
+                    for (int pp = 0; pp < P; ++pp) ar[pp][i] = fma2(A, vr[pp][j], ar[pp][i]);
+#pragma unroll
+                    for (int pp = 0; pp < P; ++pp) ai[pp][i] = fma2(A, vi[pp][j], ai[pp][i]);
+#pragma unroll
+                    for (int pp = 0; pp < P; ++pp) ar[pp][i] = fma2(B, vi[pp][j], ar[pp][i]);
+#pragma unroll
+                    for (int pp = 0; pp < P; ++pp) ai[pp][i] = fma2(C, vr[pp][j], ai[pp][i]);
                 }
         } else {
 #pragma unroll
@@ -248,10 +251,357 @@ struct BundleHops {
     }
 };
 
+// Compact form of the same hop loop: the direction mu is a runtime loop (the
+// four hops of a direction are unrolled), which keeps the kernel's code a
+// quarter of the fully unrolled size, and each hop converts and multiplies
+// one colour j of the neighbour bundle at a time, so only that colour's
+// packed pairs are live beside the accumulators. The link of the next hop
+// (and with SD = 1 the next hop's neighbour chunks) is loaded before the
+// current hop is multiplied, across direction boundaries too.
+template <typename S, typename LS, int RU, int RN, int R, int SD>
+struct BundleHopsCompact {
+    using LC = typename Traits<LS>::C;
+    static constexpr int W = Bundle<S>::W;
+    static constexpr int NG = R / W;
+    static constexpr int P = R / 2;
+    static constexpr int NCU = (RU == 18) ? 9 : (RU == 14 ? 7 : 6);
+    static constexpr int NCN = (RN == 18) ? 9 : (RN == 14 ? 7 : 6);
+    static constexpr int NCMAX = NCU > NCN ? NCU : NCN;
+
+    struct Raw {
+        LC l[NCMAX];
+        uint4 v[3][NG];
+    };
+
+    const DslashArgs& a;
+    const LC* __restrict__ Ub;
+    const LC* __restrict__ Nb;
+    const uint4* __restrict__ in;
+    int vh, p, q, h, hrow, x, y, z, t;
+    f2x (&ar)[P][3];
+    f2x (&ai)[P][3];
+
+    __device__ __forceinline__ BundleHopsCompact(const DslashArgs& args, int h_, int k0, f2x (&ar_)[P][3],
+                                                 f2x (&ai_)[P][3])
+        : a(args), ar(ar_), ai(ai_) {
+        Ub = reinterpret_cast<const LC*>(a.U);
+        Nb = reinterpret_cast<const LC*>(a.N);
+        vh = a.g.vh;
+        in = reinterpret_cast<const uint4*>(a.in[0]) + (size_t)(k0 / W) * 3 * vh;
+        p = a.parity;
+        q = 1 - p;
+        h = h_;
+        const int xh = h % a.g.hx;
+        int r = h / a.g.hx;
+        y = r % a.g.L[1];
+        r /= a.g.L[1];
+        z = r % a.g.L[2];
+        t = r / a.g.L[2];
+        x = 2 * xh + ((p + y + z + t) & 1);
+        hrow = h - xh;
+    }
+
+    __device__ __forceinline__ int coord(int mu) const { return mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t; }
+
+    template <int HOP>
+    __device__ __forceinline__ int neighbour(int mu) const {
+        constexpr int D = HOP == 0 ? 1 : HOP == 1 ? -1 : HOP == 2 ? 3 : -3;
+        const int c = coord(mu);
+        const int cn = wrap(c + D, a.g.L[mu]);
+        if (mu == 0) return hrow + (cn >> 1);
+        const int stride = mu == 1 ? a.g.sy : mu == 2 ? a.g.sz : a.g.st;
+        return h + (cn - c) * stride;
+    }
+
+    template <int HOP>
+    __device__ __forceinline__ void issue_link(int mu, Raw& b) const {
+        constexpr bool NAIK = HOP >= 2;
+        constexpr bool BACK = HOP & 1;
+        constexpr int NC = NAIK ? NCN : NCU;
+        const LC* base = (NAIK ? Nb : Ub) + (size_t)((BACK ? q : p) * 4 + mu) * NC * vh;
+        const int li = BACK ? neighbour<HOP>(mu) : h;
+        load_link_raw<LC, NC>(b.l, base, vh, li);
+    }
+
+    template <int HOP>
+    __device__ __forceinline__ void issue_spin(int mu, Raw& b) const {
+        const int hn = neighbour<HOP>(mu);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int g = 0; g < NG; ++g) b.v[c][g] = __ldg(in + (size_t)(g * 3 + c) * vh + hn);
+    }
+
+    template <int HOP>
+    __device__ __forceinline__ void compute(int mu, const Raw& b) {
+        constexpr bool NAIK = HOP >= 2;
+        constexpr bool BACK = HOP & 1;
+        constexpr int REC = NAIK ? RN : RU;
+        constexpr int NC = NAIK ? NCN : NCU;
+        const float* sc = NAIK ? a.lscale_n : a.lscale_u;
+        Link<float2> m;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
+        if constexpr (REC == 18) {
+#pragma unroll
+            for (int c = 6; c < 9; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
+        } else if constexpr (REC == 14) {
+            third_row(m, link_elem(b.l[NC - 1], sc[NC - 1]));
+        } else {
+            const int e = mu == 0 ? 0 : mu == 1 ? x : mu == 2 ? (x + y) : (x + y + z);
+            int sgn = (e & 1) ? -1 : 1;
+            if (mu == 3 && ((HOP == 0 && t == a.g.L[3] - 1) || (HOP == 1 && t == 0))) sgn = -sgn;
+            const float inv_s = (float)a.r12_inv_scale;
+            third_row(m, make_float2(sgn > 0 ? inv_s : -inv_s, 0.f));
+        }
+        if (mu == 3 && a.has_mu) {
+            const double f = HOP == 0 ? a.ft1 : HOP == 1 ? a.bt1 : HOP == 2 ? a.ft3 : a.bt3;
+            scale_link(m, (float)f);
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            f2x vr[P], vi[P];
+#pragma unroll
+            for (int pp = 0; pp < P; ++pp) chunk_pair(b.v[j][(2 * pp) / W], ((2 * pp) % W) / 2, vr[pp], vi[pp], S{});
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float2 e = BACK ? m.e[3 * j + i] : m.e[3 * i + j];
+                const f2x A = BACK ? pk2(-e.x, -e.x) : pk2(e.x, e.x);
+                const f2x B = pk2(-e.y, -e.y);
+                const f2x C = pk2(e.y, e.y);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ar[pp][i] = fma2(A, vr[pp], ar[pp][i]);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ai[pp][i] = fma2(A, vi[pp], ai[pp][i]);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ar[pp][i] = fma2(B, vi[pp], ar[pp][i]);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ai[pp][i] = fma2(C, vr[pp], ai[pp][i]);
+            }
+        }
+    }
+
+    // hop HOP of direction mu: first the look-ahead loads (the next hop's
+    // link, and with SD its neighbour chunks), then this hop's
+    template <int HOP>
+    __device__ __forceinline__ void step(int mu, Raw (&buf)[2]) {
+        constexpr int NEXT = (HOP + 1) & 3;
+        const int nmu = HOP == 3 ? mu + 1 : mu;
+        if (nmu < 4) {
+            issue_link<NEXT>(nmu, buf[NEXT & 1]);
+            if constexpr (SD == 1) issue_spin<NEXT>(nmu, buf[NEXT & 1]);
+        }
+        if constexpr (SD == 0) issue_spin<HOP>(mu, buf[HOP & 1]);
+        compute<HOP>(mu, buf[HOP & 1]);
+    }
+
+    __device__ __forceinline__ void run() {
+        Raw buf[2];
+        issue_link<0>(0, buf[0]);
+        if constexpr (SD == 1) issue_spin<0>(0, buf[0]);
+#pragma unroll 1
+        for (int mu = 0; mu < 4; ++mu) {
+            step<0>(mu, buf);
+            step<1>(mu, buf);
+            step<2>(mu, buf);
+            step<3>(mu, buf);
+        }
+    }
+};
+
+// Hop loop with the neighbour chunks staged through shared memory: every
+// thread copies the chunks of hop e + D into its own slots of a ring of
+// D + 1 stages with per-thread asynchronous 16-byte copies (cp.async, L1
+// bypassed), so the copies in flight hold no registers; hop e then reads its
+// chunks back one colour at a time. Slot (stage s, chunk c) of thread t sits
+// at ((s * 3 NG + c) * T + t) * 16 bytes, T the block's thread count:
+// consecutive threads touch consecutive 16-byte words (no bank conflicts).
+// The link of the next hop is loaded into registers one hop ahead.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename S, typename LS, int RU, int RN, int R, int D>
+struct BundleHopsStaged {
+    using LC = typename Traits<LS>::C;
+    static constexpr int W = Bundle<S>::W;
+    static constexpr int NG = R / W;
+    static constexpr int P = R / 2;
+    static constexpr int NCU = (RU == 18) ? 9 : (RU == 14 ? 7 : 6);
+    static constexpr int NCN = (RN == 18) ? 9 : (RN == 14 ? 7 : 6);
+    static constexpr int NCMAX = NCU > NCN ? NCU : NCN;
+    static constexpr int NS = D + 1;   // stages in the ring
+
+    struct Lk {
+        LC l[NCMAX];
+    };
+
+    const DslashArgs& a;
+    const LC* __restrict__ Ub;
+    const LC* __restrict__ Nb;
+    const uint4* __restrict__ in;
+    uint32_t slot0;   // shared address of this thread's chunk (stage 0, chunk 0)
+    uint32_t tstride; // bytes between consecutive chunks of one thread: 16 T
+    int vh, p, q, h, hrow, x, y, z, t;
+    f2x (&ar)[P][3];
+    f2x (&ai)[P][3];
+
+    __device__ __forceinline__ BundleHopsStaged(const DslashArgs& args, int h_, int k0, uint32_t slot0_,
+                                                uint32_t tstride_, f2x (&ar_)[P][3], f2x (&ai_)[P][3])
+        : a(args), slot0(slot0_), tstride(tstride_), ar(ar_), ai(ai_) {
+        Ub = reinterpret_cast<const LC*>(a.U);
+        Nb = reinterpret_cast<const LC*>(a.N);
+        vh = a.g.vh;
+        in = reinterpret_cast<const uint4*>(a.in[0]) + (size_t)(k0 / W) * 3 * vh;
+        p = a.parity;
+        q = 1 - p;
+        h = h_;
+        const int xh = h % a.g.hx;
+        int r = h / a.g.hx;
+        y = r % a.g.L[1];
+        r /= a.g.L[1];
+        z = r % a.g.L[2];
+        t = r / a.g.L[2];
+        x = 2 * xh + ((p + y + z + t) & 1);
+        hrow = h - xh;
+    }
+
+    template <int MU>
+    __device__ __forceinline__ int coord() const {
+        return MU == 0 ? x : MU == 1 ? y : MU == 2 ? z : t;
+    }
+
+    template <int E>
+    __device__ __forceinline__ int neighbour() const {
+        constexpr int MU = E >> 2, HOP = E & 3;
+        constexpr int DD = HOP == 0 ? 1 : HOP == 1 ? -1 : HOP == 2 ? 3 : -3;
+        const int c = coord<MU>();
+        const int cn = wrap(c + DD, a.g.L[MU]);
+        if (MU == 0) return hrow + (cn >> 1);
+        const int stride = MU == 1 ? a.g.sy : MU == 2 ? a.g.sz : a.g.st;
+        return h + (cn - c) * stride;
+    }
+
+    template <int E>
+    __device__ __forceinline__ void issue_link(Lk& b) const {
+        constexpr int MU = E >> 2, HOP = E & 3;
+        constexpr bool NAIK = HOP >= 2;
+        constexpr bool BACK = HOP & 1;
+        constexpr int NC = NAIK ? NCN : NCU;
+        const LC* base = (NAIK ? Nb : Ub) + (size_t)((BACK ? q : p) * 4 + MU) * NC * vh;
+        const int li = BACK ? neighbour<E>() : h;
+        load_link_raw<LC, NC>(b.l, base, vh, li);
+    }
+
+    // asynchronous copies of hop E's neighbour chunks into stage E % NS, one group
+    template <int E>
+    __device__ __forceinline__ void stage(int) const {
+        const int hn = neighbour<E>();
+        const uint32_t st = slot0 + (uint32_t)((E % NS) * 3 * NG) * tstride;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+                cp_async16(st + (uint32_t)(c * NG + g) * tstride, in + (size_t)(g * 3 + c) * vh + hn);
+        cp_async_commit();
+    }
+
+    template <int E>
+    __device__ __forceinline__ void compute(const Lk& b) {
+        constexpr int MU = E >> 2, HOP = E & 3;
+        constexpr bool NAIK = HOP >= 2;
+        constexpr bool BACK = HOP & 1;
+        constexpr int REC = NAIK ? RN : RU;
+        constexpr int NC = NAIK ? NCN : NCU;
+        const float* sc = NAIK ? a.lscale_n : a.lscale_u;
+        Link<float2> m;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
+        if constexpr (REC == 18) {
+#pragma unroll
+            for (int c = 6; c < 9; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
+        } else if constexpr (REC == 14) {
+            third_row(m, link_elem(b.l[NC - 1], sc[NC - 1]));
+        } else {
+            const int e = MU == 0 ? 0 : MU == 1 ? x : MU == 2 ? (x + y) : (x + y + z);
+            int sgn = (e & 1) ? -1 : 1;
+            if (MU == 3 && ((HOP == 0 && t == a.g.L[3] - 1) || (HOP == 1 && t == 0))) sgn = -sgn;
+            const float inv_s = (float)a.r12_inv_scale;
+            third_row(m, make_float2(sgn > 0 ? inv_s : -inv_s, 0.f));
+        }
+        if (MU == 3 && a.has_mu) {
+            const double f = HOP == 0 ? a.ft1 : HOP == 1 ? a.bt1 : HOP == 2 ? a.ft3 : a.bt3;
+            scale_link(m, (float)f);
+        }
+        const uint32_t st = slot0 + (uint32_t)((E % NS) * 3 * NG) * tstride;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            uint4 ch[NG];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const uint32_t ad = st + (uint32_t)(j * NG + g) * tstride;
+                asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(ch[g].x), "=r"(ch[g].y), "=r"(ch[g].z), "=r"(ch[g].w)
+                             : "r"(ad));
+            }
+            f2x vr[P], vi[P];
+#pragma unroll
+            for (int pp = 0; pp < P; ++pp) chunk_pair(ch[(2 * pp) / W], ((2 * pp) % W) / 2, vr[pp], vi[pp], S{});
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float2 e = BACK ? m.e[3 * j + i] : m.e[3 * i + j];
+                const f2x A = BACK ? pk2(-e.x, -e.x) : pk2(e.x, e.x);
+                const f2x B = pk2(-e.y, -e.y);
+                const f2x C = pk2(e.y, e.y);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ar[pp][i] = fma2(A, vr[pp], ar[pp][i]);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ai[pp][i] = fma2(A, vi[pp], ai[pp][i]);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ar[pp][i] = fma2(B, vi[pp], ar[pp][i]);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ai[pp][i] = fma2(C, vr[pp], ai[pp][i]);
+            }
+        }
+    }
+
+    template <int E>
+    __device__ __forceinline__ void step(Lk (&lk)[2]) {
+        if constexpr (E + 1 < 16) issue_link<E + 1>(lk[(E + 1) & 1]);
+        if constexpr (E + D < 16) stage<E + D>(0);
+        // the groups committed after hop E's: min(D, 15 - E) of them may stay in flight
+        constexpr int AFTER = (15 - E) < D ? (15 - E) : D;
+        cp_async_wait<AFTER>();
+        compute<E>(lk[E & 1]);
+        if constexpr (E + 1 < 16) step<E + 1>(lk);
+    }
+
+    template <int I>
+    __device__ __forceinline__ void prologue() const {
+        if constexpr (I < D) {
+            stage<I>(0);
+            prologue<I + 1>();
+        }
+    }
+
+    __device__ __forceinline__ void run() {
+        Lk lk[2];
+        issue_link<0>(lk[0]);
+        prologue<0>();
+        step<0>(lk);
+    }
+};
+
 // One Dslash of parity a.parity on the bundle layout: out = D in (EPI_NONE)
 // or out = cx x + cd (D in) with optionally Re<x, out> per rhs (EPI_X), for
 // the rhs of every thread group. a.in[0], a.out[0], a.x[0] are bundle bases.
-template <typename S, typename LS, int RU, int RN, int R, int MINB, bool PK, int LD, int SD, int EPI>
+template <typename S, typename LS, int RU, int RN, int R, int MINB, bool PK, int LD, int SD, int EPI,
+          bool COMPACT, int STAGE = 0>
 __global__ void __launch_bounds__(128, MINB) dslash_bundle_kernel(const DslashArgs a) {
     constexpr int W = Bundle<S>::W;
     constexpr int NG = R / W;
@@ -289,7 +639,18 @@ __global__ void __launch_bounds__(128, MINB) dslash_bundle_kernel(const DslashAr
         for (int k = 0; k < R; ++k)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[k][c] = make_float2(0.f, 0.f);
-        {
+        if constexpr (STAGE > 0) {
+            extern __shared__ __align__(16) unsigned char bundle_smem[];
+            const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+            const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(bundle_smem));
+            BundleHopsStaged<S, LS, RU, RN, R, STAGE> hops(a, h, k0, base + 16u * tid,
+                                                           16u * blockDim.x * blockDim.y, ar, ai);
+            hops.run();
+        } else if constexpr (COMPACT) {
+            static_assert(PK, "the compact hop loop uses packed arithmetic");
+            BundleHopsCompact<S, LS, RU, RN, R, SD> hops(a, h, k0, ar, ai);
+            hops.run();
+        } else {
             BundleHops<S, LS, RU, RN, R, PK, LD, SD> hops(a, h, k0, ar, ai, acc);
             hops.run();
         }
@@ -341,7 +702,8 @@ __host__ __device__ constexpr bool bundle_shape_ok(int n, int rpt) {
     return rpt % Bundle<S>::W == 0 && rpt % 2 == 0 && n % rpt == 0 && n / rpt >= 1 && n / rpt <= 4;
 }
 
-template <typename S, typename LS, int RU, int RN, int R, int MINB, bool PK, int LD, int SD, int EPI>
+template <typename S, typename LS, int RU, int RN, int R, int MINB, bool PK, int LD, int SD, int EPI,
+          bool COMPACT, int STAGE = 0>
 cudaError_t launch_dslash_bundle(const DslashArgs& a, cudaStream_t s) {
     if (a.t_only || !bundle_shape_ok<S>(a.nrhs, R)) return cudaErrorInvalidValue;
     if (EPI == EPI_NONE && a.red_mode != RED_NONE) return cudaErrorInvalidValue;
@@ -349,15 +711,18 @@ cudaError_t launch_dslash_bundle(const DslashArgs& a, cudaStream_t s) {
     if (G > 4) return cudaErrorInvalidValue;
     const int bx = 128 / G;   // 128 threads: 128 / G sites x G rhs groups
     const dim3 block(bx, G);
-    auto* kern = dslash_bundle_kernel<S, LS, RU, RN, R, MINB, PK, LD, SD, EPI>;
+    auto* kern = dslash_bundle_kernel<S, LS, RU, RN, R, MINB, PK, LD, SD, EPI, COMPACT, STAGE>;
+    // staged: (STAGE + 1) stages x 3 R / W chunks of 16 bytes per thread
+    const size_t smem = STAGE > 0 ? (size_t)(STAGE + 1) * 3 * (R / Bundle<S>::W) * 16 * 128 : 0;
+    static OccCache cache;   // this kernel instance's occupancy per device
     int occ = 0;
-    cudaError_t e = cached_occupancy(kern, bx * G, 0, 0, &occ);
+    cudaError_t e = cached_occupancy(cache, kern, bx * G, smem, G, &occ);
     if (e != cudaSuccess) return e;
     long long nblk = ((long long)a.g.vh + bx - 1) / bx;
     const long long cap = (long long)occ * device_sm_count();
     if (nblk > cap) nblk = cap;
     if (nblk > kMaxRedBlocks) nblk = kMaxRedBlocks;
-    kern<<<(unsigned)nblk, block, 0, s>>>(a);
+    kern<<<(unsigned)nblk, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 

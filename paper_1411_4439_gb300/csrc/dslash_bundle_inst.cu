@@ -15,38 +15,51 @@
 
 namespace hisq {
 
-// kind -> (packed arithmetic, link look-ahead, neighbour look-ahead)
-#define HISQ_B(R, B, PK, LD, SD) \
-    launch_dslash_bundle<S, LS, HISQ_RU, HISQ_RN, R, B, PK, LD, SD, EPI>(a, s)
+// kind -> hop loop: 5 unrolled, next link ahead; 6 unrolled, next link and
+// neighbours ahead; 9 compact, next link ahead; 10 compact, next link and
+// neighbours ahead
+#define HISQ_B(R, B, SD, COMPACT) \
+    launch_dslash_bundle<S, LS, HISQ_RU, HISQ_RN, R, B, true, 1, SD, EPI, COMPACT>(a, s)
+#define HISQ_BS(R, B, D) launch_dslash_bundle<S, LS, HISQ_RU, HISQ_RN, R, B, true, 1, 0, EPI, false, D>(a, s)
 
 template <int EPI>
 static cudaError_t bundle_by_variant(const DslashArgs& a, int rpt, int minb, int kind, cudaStream_t s) {
     using S = HISQ_STORE;
     using LS = HISQ_LSTORE;
-    const int key = rpt * 100 + minb * 10 + kind;
+    const int key = rpt * 1000 + minb * 100 + kind;
     switch (key) {
-        case 825: return HISQ_B(8, 2, true, 1, 0);
-        case 435: return HISQ_B(4, 3, true, 1, 0);
+        case 8305: return HISQ_B(8, 3, 0, false);
+        case 4405: return HISQ_B(4, 4, 0, false);
+        case 8309: return HISQ_B(8, 3, 0, true);
 #if HISQ_BUNDLE_FULL
-        case 815: return HISQ_B(8, 1, true, 1, 0);
-        case 835: return HISQ_B(8, 3, true, 1, 0);
-        case 445: return HISQ_B(4, 4, true, 1, 0);
-        case 816: return HISQ_B(8, 1, true, 1, 1);
-        case 826: return HISQ_B(8, 2, true, 1, 1);
-        case 436: return HISQ_B(4, 3, true, 1, 1);
-        case 827: return HISQ_B(8, 2, false, 1, 0);
-        case 837: return HISQ_B(8, 3, false, 1, 0);
-        case 437: return HISQ_B(4, 3, false, 1, 0);
-        case 447: return HISQ_B(4, 4, false, 1, 0);
-        case 828: return HISQ_B(8, 2, true, 0, 0);
-        case 838: return HISQ_B(8, 3, true, 0, 0);
-        case 448: return HISQ_B(4, 4, true, 0, 0);
+        case 8205: return HISQ_B(8, 2, 0, false);
+        case 4305: return HISQ_B(4, 3, 0, false);
+        case 4409: return HISQ_B(4, 4, 0, true);
+        case 8105: return HISQ_B(8, 1, 0, false);
+        case 8106: return HISQ_B(8, 1, 1, false);
+        case 8206: return HISQ_B(8, 2, 1, false);
+        case 4306: return HISQ_B(4, 3, 1, false);
+        case 8209: return HISQ_B(8, 2, 0, true);
+        case 8409: return HISQ_B(8, 4, 0, true);
+        case 4309: return HISQ_B(4, 3, 0, true);
+        case 8210: return HISQ_B(8, 2, 1, true);
+        case 8310: return HISQ_B(8, 3, 1, true);
+        case 4310: return HISQ_B(4, 3, 1, true);
+        case 4410: return HISQ_B(4, 4, 1, true);
+        // neighbour chunks staged in shared memory D hops ahead: kind 11 (D = 1), 12 (D = 2)
+        case 8211: return HISQ_BS(8, 2, 1);
+        case 8311: return HISQ_BS(8, 3, 1);
+        case 8411: return HISQ_BS(8, 4, 1);
+        case 8212: return HISQ_BS(8, 2, 2);
+        case 8312: return HISQ_BS(8, 3, 2);
+        case 4411: return HISQ_BS(4, 4, 1);
 #endif
         default: return cudaErrorInvalidValue;
     }
 }
 
 #undef HISQ_B
+#undef HISQ_BS
 
 cudaError_t HISQ_FAMILY(const DslashArgs& a, int epi, int rpt, int minb, int kind, cudaStream_t s) {
     switch (epi) {

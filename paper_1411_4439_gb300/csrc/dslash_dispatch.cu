@@ -36,17 +36,18 @@ cudaError_t dslash_f16_14_14_bundle(const DslashArgs&, int, int, int, int, cudaS
 
 int dslash_max_rpt(int prec) { return prec == HISQ_F64 ? 4 : 8; }
 
-// (rpt, minb, kind) keys of the bundle kernels: every family has the default
+// (rpt, minb, kind) of the bundle kernels: every family has the default
 // mappings; the U r18 / N r14 families (the configurations' compression) also
 // the variants the autotuner chooses from.
 bool bundle_mapping_built(int prec, int ru, int rn, int rpt, int minb, int kind) {
     if (prec != HISQ_F32 && prec != HISQ_F16) return false;
-    const int key = rpt * 100 + minb * 10 + kind;
-    if (key == 825 || key == 435) return true;
+    const int key = rpt * 1000 + minb * 100 + kind;
+    if (key == 8305 || key == 4405 || key == 8309) return true;
     if (!(ru == 18 && rn == 14)) return false;
     switch (key) {
-        case 815: case 835: case 445: case 816: case 826: case 436: case 827: case 837: case 437:
-        case 447: case 828: case 838: case 448:
+        case 8205: case 4305: case 4409: case 8105: case 8106: case 8206: case 4306: case 8209: case 8409: case 4309:
+        case 8210: case 8310: case 4310: case 4410: case 8211: case 8311: case 8411: case 8212: case 8312:
+        case 4411:
             return true;
         default:
             return false;
@@ -66,10 +67,10 @@ DslashTune dslash_bundle_tune(int prec, int n) {
     if (W == 0 || n % W != 0) return t;
     if (n % 8 == 0 && n / 8 <= 4) {
         t.rpt = 8;
-        t.minb = 2;
+        t.minb = 3;
     } else if (n % 4 == 0 && n / 4 <= 4) {
         t.rpt = 4;
-        t.minb = 3;
+        t.minb = 4;
     }
     return t;
 }

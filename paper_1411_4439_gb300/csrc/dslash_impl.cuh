@@ -527,27 +527,56 @@ __device__ __forceinline__ void block_reduce_finish(const DslashArgs& a, int k0,
     }
 }
 
-// Resident blocks per SM of a kernel, cached per device (the first call on a
-// device measures it; every later call reads it).
-// The first call on a device also sets the kernel's shared-memory attribute
-// there: the whole SRAM as L1 when smem == 0 (the kernels gather their
-// neighbour vectors through L1), else the dynamic shared memory size.
+// Resident blocks per SM of one kernel, cached per device: every launcher
+// (one per kernel instance) owns its cache and passes it in; the first call
+// on a device measures the occupancy and sets the kernel's shared-memory
+// attribute there. Kernels without dynamic shared memory (smem == 0) gather
+// their neighbour vectors through L1, so they get the smallest shared-memory
+// carveout that still holds as many blocks as their registers allow (the
+// few KB of static reduction buffers per block would otherwise cap a
+// zero carveout at two blocks); the rest of the SRAM is L1.
+struct OccCache {
+    std::atomic<int> v[64][16];
+};
+
 template <typename K>
-cudaError_t cached_occupancy(K* kern, int threads, size_t smem, int slot, int* occ) {
-    static std::atomic<int> cache[64][16];
+cudaError_t cached_occupancy(OccCache& cache, K* kern, int threads, size_t smem, int slot, int* occ) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || slot < 0 || slot >= 16) return cudaErrorInvalidValue;
-    int v = cache[dev][slot].load(std::memory_order_relaxed);
+    int v = cache.v[dev][slot].load(std::memory_order_relaxed);
     if (v == 0) {
-        e = smem == 0 ? cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0)
-                      : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem);
-        if (e != cudaSuccess) return e;
+        if (smem == 0) {
+            // the largest occupancy any carveout reaches, then the smallest
+            // carveout (percent of the maximum shared memory) that reaches it
+            const int carveouts[] = {0, 4, 8, 12, 16, 25, 50, 100};
+            int occ_at[8] = {0};
+            int best = 0;
+            for (int i = 0; i < 8; ++i) {
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carveouts[i]);
+                if (e != cudaSuccess) return e;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_at[i], kern, threads, 0);
+                if (e != cudaSuccess) return e;
+                if (occ_at[i] > best) best = occ_at[i];
+            }
+            int pick = 7;
+            for (int i = 0; i < 8; ++i)
+                if (occ_at[i] == best) {
+                    pick = i;
+                    break;
+                }
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carveouts[pick]);
+            if (e != cudaSuccess) return e;
+            v = best;
+        } else {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem);
+            if (e != cudaSuccess) return e;
+        }
         if (v < 1) v = 1;
-        cache[dev][slot].store(v, std::memory_order_relaxed);
+        cache.v[dev][slot].store(v, std::memory_order_relaxed);
     }
     *occ = v;
     return cudaSuccess;
@@ -564,8 +593,9 @@ cudaError_t launch_dslash_instance(const DslashArgs& a, cudaStream_t s) {
     bx &= ~31;
     const dim3 block(bx, G);
     auto* kern = dslash_kernel<S, LS, RU, RN, RPT, MINB, EPI, LAYOUT, PACK>;
+    static OccCache cache;   // this kernel instance's occupancy per device
     int occ = 0;
-    cudaError_t e = cached_occupancy(kern, bx * G, 0, G, &occ);
+    cudaError_t e = cached_occupancy(cache, kern, bx * G, 0, G, &occ);
     if (e != cudaSuccess) return e;
     long long nblk = ((long long)a.g.vh + bx - 1) / bx;
     long long cap = (long long)occ * device_sm_count();

@@ -253,8 +253,9 @@ cudaError_t launch_dslash_pipe(const DslashArgs& a, cudaStream_t s) {
     bx &= ~31;
     const dim3 block(bx, G);
     auto* kern = dslash_pipe_kernel<S, LS, RU, RN, RPT, MINB, DEPTH, EPI, LAYOUT>;
+    static OccCache cache;   // this kernel instance's occupancy per device
     int occ = 0;
-    cudaError_t e = cached_occupancy(kern, bx * G, 0, G, &occ);
+    cudaError_t e = cached_occupancy(cache, kern, bx * G, 0, G, &occ);
     if (e != cudaSuccess) return e;
     long long nblk = ((long long)a.g.vh + bx - 1) / bx;
     long long cap = (long long)occ * device_sm_count();

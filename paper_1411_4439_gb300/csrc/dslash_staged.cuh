@@ -361,8 +361,9 @@ cudaError_t launch_dslash_staged(const DslashArgs& a, cudaStream_t s) {
     const dim3 block(kStagedTile, G);
     const size_t smem = 2ull * 2 * (NCU + NCN) * kStagedTile * sizeof(LC);
     auto* kern = dslash_staged_kernel<S, LS, RU, RN, RPT, MINB, EPI, LAYOUT>;
+    static OccCache cache;   // this kernel instance's occupancy per device
     int occ = 0;
-    cudaError_t e = cached_occupancy(kern, kStagedTile * G, smem, G, &occ);
+    cudaError_t e = cached_occupancy(cache, kern, kStagedTile * G, smem, G, &occ);
     if (e != cudaSuccess) return e;
     long long nblk = a.g.vh / kStagedTile;
     const long long cap = (long long)occ * device_sm_count();

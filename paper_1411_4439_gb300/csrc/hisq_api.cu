@@ -367,11 +367,10 @@ extern "C" hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rpt, int minb, 
         return fail(HISQ_EINVAL, "rhs per thread must be 0 (auto), 1, 2, 4 or 8");
     if (minb < 0 || minb > 8) return fail(HISQ_EINVAL, "min blocks per SM must be 0 (auto) .. 8");
     if (flags & ~(HISQ_MAP_PACKED | HISQ_MAP_L2_PREFETCH | HISQ_MAP_STAGED | HISQ_MAP_PIPELINED |
-                  HISQ_MAP_PIPELINED2 | HISQ_MAP_SCALAR | HISQ_MAP_NO_LOOKAHEAD))
+                  HISQ_MAP_PIPELINED2 | HISQ_MAP_COMPACT))
         return fail(HISQ_EINVAL, "unknown mapping flags %d", flags);
     const int kinds = !!(flags & HISQ_MAP_PACKED) + !!(flags & HISQ_MAP_STAGED) +
-                      !!(flags & HISQ_MAP_PIPELINED) + !!(flags & HISQ_MAP_PIPELINED2) +
-                      !!(flags & HISQ_MAP_SCALAR) + !!(flags & HISQ_MAP_NO_LOOKAHEAD);
+                      !!(flags & HISQ_MAP_PIPELINED) + !!(flags & HISQ_MAP_PIPELINED2);
     if (kinds > 1) return fail(HISQ_EINVAL, "mapping flags %d name more than one kernel kind", flags);
     g->tune_rpt = rpt;
     g->tune_minb = minb;
@@ -472,18 +471,18 @@ int kind_of_flags(int flags) {
 }
 
 int bundle_kind_of_flags(int flags) {
-    if (flags & HISQ_MAP_SCALAR) return KIND_BUNDLE_SCALAR;
-    if (flags & HISQ_MAP_NO_LOOKAHEAD) return KIND_BUNDLE_NOLA;
-    if (flags & (HISQ_MAP_PIPELINED | HISQ_MAP_PIPELINED2)) return KIND_BUNDLE_SPIN;
-    return KIND_BUNDLE;
+    if (flags & HISQ_MAP_STAGED) return (flags & HISQ_MAP_PIPELINED2) ? KIND_BUNDLE_SMEM2 : KIND_BUNDLE_SMEM1;
+    const bool spin = flags & (HISQ_MAP_PIPELINED | HISQ_MAP_PIPELINED2);
+    if (flags & HISQ_MAP_COMPACT) return spin ? KIND_BUNDLE_COMPACT_SPIN : KIND_BUNDLE_COMPACT;
+    return spin ? KIND_BUNDLE_SPIN : KIND_BUNDLE;
 }
 
 int flags_of_tune(const DslashTune& t) {
+    if (t.layout == HISQ_BUNDLE && (t.kind == KIND_BUNDLE_SMEM1 || t.kind == KIND_BUNDLE_SMEM2))
+        return HISQ_MAP_STAGED | (t.kind == KIND_BUNDLE_SMEM2 ? HISQ_MAP_PIPELINED2 : 0);
     if (t.layout == HISQ_BUNDLE)
-        return t.kind == KIND_BUNDLE_SCALAR ? HISQ_MAP_SCALAR
-               : t.kind == KIND_BUNDLE_NOLA ? HISQ_MAP_NO_LOOKAHEAD
-               : t.kind == KIND_BUNDLE_SPIN ? HISQ_MAP_PIPELINED
-                                            : 0;
+        return (t.kind == KIND_BUNDLE_COMPACT || t.kind == KIND_BUNDLE_COMPACT_SPIN ? HISQ_MAP_COMPACT : 0) |
+               (t.kind == KIND_BUNDLE_SPIN || t.kind == KIND_BUNDLE_COMPACT_SPIN ? HISQ_MAP_PIPELINED : 0);
     const int k = t.kind == KIND_PACKED   ? HISQ_MAP_PACKED
                   : t.kind == KIND_STAGED ? HISQ_MAP_STAGED
                   : t.kind == KIND_PIPE1  ? HISQ_MAP_PIPELINED
@@ -507,7 +506,7 @@ DslashTune pick_tune(hisq_gauge g, int n, int prec, int requested, int layout) {
         const int ru = link_recon_u(g, prec), rn = link_recon_n(g, prec);
         const int r = requested ? requested : g->tune_rpt;
         if (r && n % r == 0 && n / r <= 4) {
-            const int b = (!requested && g->tune_minb) ? g->tune_minb : (r == 8 ? 2 : 3);
+            const int b = (!requested && g->tune_minb) ? g->tune_minb : (r == 8 ? 3 : 4);
             const int k = requested ? KIND_BUNDLE : bundle_kind_of_flags(g->tune_flags);
             if (bundle_mapping_built(prec, ru, rn, r, b, k)) {
                 t.rpt = r;
@@ -748,7 +747,8 @@ std::vector<DslashTune> candidate_tunes(hisq_gauge g, int n, int prec, int layou
     std::vector<DslashTune> out;
     if (layout == HISQ_BUNDLE) {
         const int ru = link_recon_u(g, prec), rn = link_recon_n(g, prec);
-        const int kinds[] = {KIND_BUNDLE, KIND_BUNDLE_SPIN, KIND_BUNDLE_SCALAR, KIND_BUNDLE_NOLA};
+        const int kinds[] = {KIND_BUNDLE, KIND_BUNDLE_SPIN, KIND_BUNDLE_COMPACT, KIND_BUNDLE_COMPACT_SPIN,
+                             KIND_BUNDLE_SMEM1, KIND_BUNDLE_SMEM2};
         for (int r : {4, 8}) {
             if (n % r != 0 || n / r > 4) continue;
             for (int b = 1; b <= 4; ++b)

@@ -226,12 +226,15 @@ enum Epi : int { EPI_NONE = 0, EPI_X = 1, EPI_XY = 2 };
 // the register kernel, 1 the register kernel with packed f32x2 complex
 // arithmetic (FP32 arithmetic only), 2 the kernel with links staged in shared
 // memory by bulk copies (FP32 arithmetic only).
-// Kinds 5 to 8 run on the bundle spinor layout (dslash_bundle.cuh): packed
-// f32x2 arithmetic with the next hop's link in flight (5), also the next
-// hop's neighbours in flight (6), scalar arithmetic (7), no look-ahead (8).
+// Kinds 5, 6 and 9 to 12 run on the bundle spinor layout (dslash_bundle.cuh),
+// with packed f32x2 arithmetic and the next hop's link in flight: the fully
+// unrolled hop loop (5), also the next hop's neighbours in flight (6), the
+// compact hop loop (9), compact with the neighbours in flight (10), and the
+// neighbour chunks copied into shared memory one (11) or two (12) hops ahead.
 enum DslashKind : int {
     KIND_REG = 0, KIND_PACKED = 1, KIND_STAGED = 2, KIND_PIPE1 = 3, KIND_PIPE2 = 4,
-    KIND_BUNDLE = 5, KIND_BUNDLE_SPIN = 6, KIND_BUNDLE_SCALAR = 7, KIND_BUNDLE_NOLA = 8
+    KIND_BUNDLE = 5, KIND_BUNDLE_SPIN = 6, KIND_BUNDLE_COMPACT = 9, KIND_BUNDLE_COMPACT_SPIN = 10,
+    KIND_BUNDLE_SMEM1 = 11, KIND_BUNDLE_SMEM2 = 12
 };
 struct DslashTune {
     int rpt;

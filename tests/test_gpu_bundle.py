@@ -137,10 +137,9 @@ def test_bundle_dslash_matches_oracle(gpu_lib, L, prec, ru, rn):
 
 
 # every bundle mapping built for U r18 / N r14: (rhs per thread, min blocks, flags)
-MAPPINGS = [(8, 2, 0), (4, 3, 0), (8, 1, 0), (8, 3, 0), (4, 4, 0),
-            (8, 1, 8), (8, 2, 8), (4, 3, 8),
-            (8, 2, 32), (8, 3, 32), (4, 3, 32), (4, 4, 32),
-            (8, 2, 64), (8, 3, 64), (4, 4, 64)]
+MAPPINGS = [(8, 3, 0), (4, 4, 0), (8, 3, 128), (8, 2, 0), (4, 3, 0), (4, 4, 128),
+            (8, 1, 0), (8, 1, 8), (8, 2, 8), (4, 3, 8),
+            (8, 2, 128), (8, 4, 128), (4, 3, 128), (8, 2, 136), (8, 3, 136), (4, 3, 136), (4, 4, 136)]
 
 
 @pytest.mark.parametrize("prec", [1, 2])
