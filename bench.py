@@ -964,6 +964,40 @@ def run_dslash_probe(args):
     H.hisq_gauge_free(g)
 
 
+def run_cg_probe(args):
+    """One solve of the headline system (48^3x12, FP16 storage, n = 8, m =
+    0.0025) capped at --maxiter iterations, for launch lists and captures of
+    the solve's kernels; prints iterations and seconds."""
+    import torch
+
+    import hisq_inputs as gen
+    import paper_1411_4439_gb300 as H
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    H.hisq.library()
+    Ls = tuple(args.lattice)
+    U, N = gen.hisq_links(Ls, seed=LINK_SEED)
+    g = H.hisq_gauge_load(Ls, torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev), prec=H.HISQ_F16,
+                          recon_U=18, recon_N=14)
+    del U, N
+    b = gen.gaussian_source(Ls, args.n, seed=SOURCE_SEED)
+    bt = [torch.from_numpy(b[k]).to(dev) for k in range(args.n)]
+    xt = [torch.zeros_like(t) for t in bt]
+    p = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=RELIABLE_EVERY, maxiter=args.maxiter)
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            st = H.hisq_cg_solve(g, MASS, 0.0, bt, xt, TOL, p, stream=stream)
+        except H.HisqError as e:      # HISQ_ENOCONV at the cap: the stats ride on the error
+            st = e.stats
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": "cg probe", "lattice": list(Ls), "n": args.n, "iterations": st.total_iters,
+                          "reliable_updates": st.reliable_updates, "s": time.perf_counter() - t0}), flush=True)
+    H.hisq_gauge_free(g)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -971,7 +1005,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["headline", "cg-configs", "dslash-sweep", "batched", "inverter-sweep",
-                                           "oracle-timing", "dslash-probe"],
+                                           "oracle-timing", "dslash-probe", "cg-probe"],
                     default="headline",
                     help="headline = the one JSON line of the contract; oracle-timing needs --impl reference")
     ap.add_argument("--lattices", default="48x48x48x12,64x64x64x16",
@@ -988,6 +1022,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--op", choices=["dslash", "mdagm"], default="dslash")
+    ap.add_argument("--maxiter", type=int, default=400, help="cg-probe: iteration cap")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":
@@ -1002,6 +1037,8 @@ def main(argv=None):
         run_inverter_sweep(args)
     elif args.workload == "dslash-probe":
         run_dslash_probe(args)
+    elif args.workload == "cg-probe":
+        run_cg_probe(args)
     else:
         run_gpu(args)
 

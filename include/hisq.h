@@ -369,13 +369,19 @@ typedef struct {
     hisq_prec inner_prec;  /* storage precision of the inner iteration (F32) */
     int use_x0;            /* 1: x holds an initial guess on entry (0) */
     int even_odd;          /* 1: even-odd system at mu = 0 (1) */
-    int check_every;       /* host convergence poll interval (10) */
+    int check_every;       /* iterations between convergence / reliable-update decisions (10) */
     int use_graphs;        /* 1: replay iterations from a captured CUDA graph (1) */
     int rhs_per_thread;    /* Dslash rhs per thread: 0 = auto, else 1/2/4/8 */
     hisq_layout spinor_layout; /* layout of the CG's internal low-precision vectors
                                   (HISQ_BUNDLE; where n is not a multiple of the
                                   chunk width, or for F64 and full-lattice solves,
                                   the solve uses HISQ_AOS) */
+    int device_loop;       /* 1: the whole solve is one graph launch whose
+                              conditional nodes take every decision on the
+                              device (needs use_graphs, and maxiter and
+                              reliable_every multiples of check_every; else
+                              the host decides after every check_every
+                              iterations) (1) */
 } hisq_cg_params;
 
 typedef struct {

@@ -145,19 +145,25 @@ struct Workspace {
     double* partials = nullptr;
     unsigned int* counter = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_body = nullptr;   // captures the device loop's body
+    cudaStream_t cap_if = nullptr;     // captures its reliable-update branch
     std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, double, double, int, int, int, double, double>, cudaGraphExec_t> loops;
     size_t bytes = 0;
 };
 
 void free_workspace(Workspace* w) {
     if (!w) return;
     for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : w->loops) cudaGraphExecDestroy(kv.second);
     void* ptrs[] = {w->r_lo, w->p_lo, w->Ap_lo, w->x_lo, w->t_lo, w->b_hi, w->x_hi,
                     w->r_hi, w->t_hi, w->cg, w->partials, w->counter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (w->cg_host) cudaFreeHost(w->cg_host);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
+    if (w->cap_body) cudaStreamDestroy(w->cap_body);
+    if (w->cap_if) cudaStreamDestroy(w->cap_if);
     delete w;
 }
 
@@ -369,8 +375,10 @@ extern "C" hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rpt, int minb, 
     if (flags & ~(HISQ_MAP_PACKED | HISQ_MAP_L2_PREFETCH | HISQ_MAP_STAGED | HISQ_MAP_PIPELINED |
                   HISQ_MAP_PIPELINED2 | HISQ_MAP_COMPACT))
         return fail(HISQ_EINVAL, "unknown mapping flags %d", flags);
+    // STAGED with PIPELINED2 selects the bundle kernel staging two hops ahead
     const int kinds = !!(flags & HISQ_MAP_PACKED) + !!(flags & HISQ_MAP_STAGED) +
-                      !!(flags & HISQ_MAP_PIPELINED) + !!(flags & HISQ_MAP_PIPELINED2);
+                      !!(flags & HISQ_MAP_PIPELINED) + !!(flags & HISQ_MAP_PIPELINED2) -
+                      ((flags & HISQ_MAP_STAGED) && (flags & HISQ_MAP_PIPELINED2) ? 1 : 0);
     if (kinds > 1) return fail(HISQ_EINVAL, "mapping flags %d name more than one kernel kind", flags);
     g->tune_rpt = rpt;
     g->tune_minb = minb;
@@ -1087,6 +1095,7 @@ extern "C" void hisq_cg_default_params(hisq_cg_params* p) {
     p->rhs_per_thread = 0;
     // the bundle layout where n fits it (F32 / F16 even-odd solves), else AoS
     p->spinor_layout = HISQ_BUNDLE;
+    p->device_loop = 1;
 }
 
 namespace {
@@ -1138,6 +1147,8 @@ hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** o
         if (e == cudaSuccess) e = cudaMemset(z, 0, hi);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&w->cg_host, sizeof(CgScalars));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap_body, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap_if, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         free_workspace(w);
         return fail(e == cudaErrorMemoryAllocation ? HISQ_ENOMEM : HISQ_ECUDA,
@@ -1146,6 +1157,89 @@ hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** o
     g->ws.push_back(w);
     *out = w;
     return HISQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device-driven iteration loop: after every chunk of iterations a one-warp
+// kernel takes the decisions the host would take (reliable update or not),
+// sets the condition of an IF node holding the reliable update, and a second
+// one-warp kernel after it books the update, detects convergence, the
+// iteration cap and breakdowns, and sets the condition of the WHILE node
+// that repeats the chunk. The host launches one graph per solve.
+// ---------------------------------------------------------------------------
+struct LoopArgs {
+    CgScalars* cg;
+    int n;
+    int chunk;
+    int maxiter;
+    int reliable_every;
+    double delta2;                        // reliable_delta^2
+    double tol2;
+    cudaGraphConditionalHandle h_if;      // runs the reliable update
+    cudaGraphConditionalHandle h_loop;    // repeats the chunk
+};
+
+__global__ void loop_decide_kernel(LoopArgs a) {
+    CgScalars* cg = a.cg;
+    const int k = threadIdx.x;
+    const int iter = cg->iter + a.chunk;
+    const int since = cg->since_rel + a.chunk;
+    int need = 0;
+    if (k < a.n) {
+        const int act = cg->active[k];
+        const int restarted = act && cg->restarts[k] != cg->seen_restarts[k];
+        cg->seen_restarts[k] = cg->restarts[k];
+        cg->restarted[k] = restarted;
+        if (act) {
+            const double sc = cg->scale[k];
+            need = cg->frozen[k] || restarted || cg->rr[k] <= a.delta2 * cg->rr_rel[k] ||
+                   cg->rr[k] <= a.tol2 * cg->bb[k] * sc * sc;
+        }
+        cg->was[k] = act;
+        cg->before[k] = cg->rr_true[k];
+    }
+    need = __any_sync(0xffffffffu, need) || since >= a.reliable_every || iter >= a.maxiter;
+    if (cg->flags) need = 0;   // the post step stops the loop
+    if (k == 0) {
+        cg->iter = iter;
+        cg->since_rel = since;
+        cg->need = need;
+        cudaGraphSetConditional(a.h_if, need ? 1u : 0u);
+    }
+}
+
+__global__ void loop_post_kernel(LoopArgs a) {
+    CgScalars* cg = a.cg;
+    const int k = threadIdx.x;
+    const int need = cg->need;
+    const int iter = cg->iter;
+    int broke = 0;
+    if (need && k < a.n) {
+        if (cg->was[k] && !cg->active[k]) cg->iters_k[k] = iter;
+        // restarts that bring no progress of the FP64 residual are a breakdown
+        const int bad = (cg->was[k] && cg->active[k] && cg->restarted[k] && !(cg->rr_true[k] < cg->before[k]))
+                            ? cg->bad_updates[k] + 1
+                            : 0;
+        cg->bad_updates[k] = bad;
+        broke = bad >= 3;
+    }
+    broke = __any_sync(0xffffffffu, broke);
+    const int any_active = __any_sync(0xffffffffu, k < a.n && cg->active[k]);
+    if (k == 0) {
+        int result = cg->result;
+        if (need) {
+            cg->reliable += 1;
+            cg->since_rel = 0;
+        }
+        if (broke) result = HISQ_EBREAKDOWN;
+        int done = !any_active || cg->flags || result != HISQ_OK;
+        if (!done && iter >= a.maxiter) {
+            result = HISQ_ENOCONV;
+            done = 1;
+        }
+        cg->result = result;
+        cudaGraphSetConditional(a.h_loop, done ? 0u : 1u);
+    }
 }
 
 struct Solver {
@@ -1353,6 +1447,75 @@ struct Solver {
         cudaError_t e = cudaMemcpyAsync(w->cg_host, w->cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         return e;
+    }
+
+    // Adds to the graph being captured on stream s a WHILE node whose body runs
+    // la.chunk iterations, the decision kernel, an IF node holding the
+    // reliable update, and the booking kernel (see loop_decide_kernel).
+    cudaError_t capture_loop(cudaStream_t s, LoopArgs la) const {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t graph = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &nd);
+        if (e != cudaSuccess) return e;
+        cudaGraphConditionalHandle h_loop;
+        e = cudaGraphConditionalHandleCreate(&h_loop, graph, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) return e;
+        // node parameters in zeroed raw storage (the struct has no default constructor)
+        alignas(cudaGraphNodeParams) unsigned char wbuf[sizeof(cudaGraphNodeParams)] = {};
+        cudaGraphNodeParams& wp = *reinterpret_cast<cudaGraphNodeParams*>(wbuf);
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = h_loop;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        e = cudaGraphAddNode(&wnode, graph, deps, nullptr, nd, &wp);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) return e;
+        cudaGraph_t body = wp.conditional.phGraph_out[0];
+        cudaGraphConditionalHandle h_if;
+        e = cudaGraphConditionalHandleCreate(&h_if, body, 0, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) return e;
+        la.h_if = h_if;
+        la.h_loop = h_loop;
+        cudaStream_t sb = w->cap_body, si = w->cap_if;
+        e = cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        for (int i = 0; i < la.chunk && e == cudaSuccess; ++i) e = iterate(sb);
+        if (e == cudaSuccess) {
+            loop_decide_kernel<<<1, 32, 0, sb>>>(la);
+            e = cudaGetLastError();
+        }
+        cudaGraph_t g2 = nullptr;
+        if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(sb, &cs, nullptr, &g2, &deps, nullptr, &nd);
+        alignas(cudaGraphNodeParams) unsigned char ibuf[sizeof(cudaGraphNodeParams)] = {};
+        cudaGraphNodeParams& ip = *reinterpret_cast<cudaGraphNodeParams*>(ibuf);
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = h_if;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t inode;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&inode, g2, deps, nullptr, nd, &ip);
+        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(sb, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) {
+            e = cudaStreamBeginCaptureToGraph(si, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e1 = reliable_update(si);
+                cudaGraph_t gi = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(si, &gi);
+                e = e1 != cudaSuccess ? e1 : e2;
+            }
+        }
+        if (e == cudaSuccess) {
+            loop_post_kernel<<<1, 32, 0, sb>>>(la);
+            e = cudaGetLastError();
+        }
+        cudaGraph_t gb = nullptr;
+        cudaError_t e3 = cudaStreamEndCapture(sb, &gb);
+        return e != cudaSuccess ? e : e3;
     }
 
     // Run `chunk` iterations, from a captured graph when enabled.
@@ -1579,6 +1742,66 @@ struct CgRun {
         return HISQ_OK;
     }
 
+    // Whether the whole solve can run as one graph launch (the chunk of the
+    // loop body divides the iteration cap and the reliable-update period).
+    bool device_loop_ok() const {
+        const int c = prm.check_every;
+        return prm.use_graphs && prm.device_loop && prm.maxiter % c == 0 &&
+               (prm.reliable_every % c == 0 || prm.reliable_every >= prm.maxiter);
+    }
+
+    LoopArgs loop_args() const {
+        LoopArgs la;
+        la.cg = w->cg;
+        la.n = n;
+        la.chunk = prm.check_every;
+        la.maxiter = prm.maxiter;
+        la.reliable_every = prm.reliable_every;
+        la.delta2 = prm.reliable_delta * prm.reliable_delta;
+        la.tol2 = sv.tol2;
+        la.h_if = la.h_loop = 0;
+        return la;
+    }
+
+    // After the device loop ended: read its book-keeping into the host state.
+    hisq_status after_device_loop(cudaStream_t s) {
+        HISQ_CUDA(sv.poll(s));
+        const CgScalars& h = *w->cg_host;
+        iter = h.iter;
+        reliable = h.reliable;
+        for (int k = 0; k < n; ++k) iters_k[k] = h.iters_k[k];
+        if (h.result != HISQ_OK && result == HISQ_OK) result = (hisq_status)h.result;
+        stop = true;
+        return HISQ_OK;
+    }
+
+    // The solve as one launch of a cached graph holding the device loop.
+    hisq_status run_device_loop(cudaStream_t s) {
+        const auto key = std::make_tuple(prm.check_every, sv.mass, sv.mu,
+                                         sv.tune.kind * 10000 + sv.tune.rpt * 100 + sv.tune.minb * 10 + sv.tune.layout,
+                                         prm.maxiter, prm.reliable_every, prm.reliable_delta, sv.tol2);
+        auto it = w->loops.find(key);
+        if (it == w->loops.end()) {
+            if (w->loops.size() >= 4) {
+                for (auto& kv : w->loops) cudaGraphExecDestroy(kv.second);
+                w->loops.clear();
+            }
+            cudaGraph_t graph = nullptr;
+            HISQ_CUDA(cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = sv.capture_loop(w->cap_stream, loop_args());
+            cudaError_t e2 = cudaStreamEndCapture(w->cap_stream, &graph);
+            HISQ_CUDA(e);
+            HISQ_CUDA(e2);
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            HISQ_CUDA(e);
+            it = w->loops.emplace(key, exec).first;
+        }
+        HISQ_CUDA(cudaGraphLaunch(it->second, s));
+        return after_device_loop(s);
+    }
+
     // Copy the solution out, fill stats and return the status of the solve.
     hisq_status finish(hisq_cg_stats* stats, cudaStream_t s) {
         if (result == HISQ_ENOCONV) {
@@ -1635,6 +1858,10 @@ extern "C" hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu, const
     CgRun run;
     st = run.start(g, mass, mu, b, x, n, tol, prm, s);
     if (st != HISQ_OK) return st;
+    if (!run.stop && run.device_loop_ok()) {
+        st = run.run_device_loop(s);
+        if (st != HISQ_OK) return st;
+    }
     while (!run.stop) {
         const int chunk = run.next_chunk();
         st = run.sv.run_chunk(chunk, prm.use_graphs != 0, s);
@@ -1694,6 +1921,34 @@ extern "C" hisq_status hisq_cg_solve_batched(const hisq_cg_problem* probs, int n
         return fail(HISQ_ECUDA, "batched solve set-up failed: %s", cudaGetErrorString(e));
     }
     hisq_status st = HISQ_OK;
+    // every unfinished problem as one device loop, all in one graph launch
+    bool dev_loop = graphs;
+    for (int i = 0; i < nprob; ++i) dev_loop = dev_loop && (runs[i].stop || runs[i].device_loop_ok());
+    if (dev_loop) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, cap);
+        for (int i = 0; i < nprob && e == cudaSuccess; ++i) {
+            if (runs[i].stop) continue;
+            cudaStream_t si = runs[i].w->cap_stream;
+            e = cudaStreamWaitEvent(si, fork, 0);
+            if (e == cudaSuccess) e = runs[i].sv.capture_loop(si, runs[i].loop_args());
+            if (e == cudaSuccess) e = cudaEventRecord(join[i], si);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join[i], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e == cudaSuccess) {
+            cache.emplace(std::make_pair(~0ull, 0), exec);
+            e = cudaGraphLaunch(exec, s);
+        }
+        if (e != cudaSuccess) st = fail(HISQ_ECUDA, "batched device loop failed: %s", cudaGetErrorString(e));
+        for (int i = 0; i < nprob && st == HISQ_OK; ++i)
+            if (!runs[i].stop) st = runs[i].after_device_loop(s);
+    }
     while (st == HISQ_OK) {
         unsigned long long mask = 0;
         int chunk = 1 << 30;

@@ -168,6 +168,18 @@ struct CgScalars {
     double freeze2;            // squared residual drop that freezes an rhs (precision safety net)
     double alpha_max;          // alpha above this bound (1/lambda_min) means lost precision: restart
     int flags;                 // kFlagBreakdown | kFlagNaN
+    // state of the device-driven iteration loop (one graph launch per solve)
+    int iter;                  // iterations run
+    int since_rel;             // iterations since the last reliable update
+    int reliable;              // reliable updates done
+    int need;                  // the last decision asked for a reliable update
+    int result;                // HISQ_OK, or HISQ_ENOCONV / HISQ_EBREAKDOWN decided on the device
+    int seen_restarts[kMaxRhs];
+    int restarted[kMaxRhs];    // restarts counted since the previous decision
+    int was[kMaxRhs];          // active before the pending reliable update
+    int bad_updates[kMaxRhs];  // consecutive restarted updates without FP64 progress
+    int iters_k[kMaxRhs];      // iteration at which rhs k converged
+    double before[kMaxRhs];    // rr_true before the pending reliable update
 };
 constexpr int kFlagBreakdown = 1;
 constexpr int kFlagNaN = 2;

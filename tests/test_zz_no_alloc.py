@@ -47,3 +47,49 @@ def test_matches_the_allocating_entry_point_on_two_calls(gpu_lib):
             assert np.allclose(got, exact, rtol=1e-12)
     finally:
         H.hisq_gauge_free(g)
+
+
+def test_rejects_non_fp64_and_host_vectors_before_any_launch():
+    import torch
+    import paper_1411_4439_gb300 as H
+    host = [np.zeros((8, 3), dtype=np.complex128)]
+    with pytest.raises(ValueError):
+        H.hisq_cdot_noalloc(host, host)          # numpy arrays are host memory
+    c64 = [torch.zeros(8, 3, dtype=torch.complex64)]
+    with pytest.raises(ValueError):
+        H.hisq_cdot_noalloc(c64, c64)
+    with pytest.raises(ValueError):
+        H.hisq_cdot(None, c64, c64)              # checked before the handle is used
+
+
+@pytest.mark.gpu
+def test_largest_block_count_and_after_a_solve_on_the_same_stream(gpu_lib):
+    """A length that launches the largest grid the reduction uses (8 blocks
+    per SM for one rhs), and a call queued right behind a CG solve on the
+    same stream (the solve's own reductions share nothing with this scratch)."""
+    import torch
+    import hisq_inputs as gen
+    H = gpu_lib
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    length = 2 * 8 * sms * 256                     # complex numbers: > 8 SMs' worth of 256-thread blocks
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal(length) + 1j * rng.standard_normal(length)
+    b = rng.standard_normal(length) + 1j * rng.standard_normal(length)
+    at, bt = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    got = H.hisq_cdot_noalloc([at], [bt])
+    assert np.allclose(got, [np.vdot(a, b)], rtol=1e-12)
+    L = (4, 6, 8, 10)
+    U, N = gen.hisq_links(L, seed=121)
+    g = H.hisq_gauge_load(L, torch.from_numpy(U).cuda(), torch.from_numpy(N).cuda(), prec=H.HISQ_F32,
+                          recon_U=18, recon_N=14)
+    try:
+        src = torch.from_numpy(gen.z2_source(L, 4, seed=122)).cuda()
+        xs = [torch.zeros_like(src[k]) for k in range(4)]
+        stream = torch.cuda.current_stream()
+        H.hisq_cg_solve(g, 0.1, 0.0, [src[k] for k in range(4)], xs, 1e-10,
+                        H.cg_params(inner_prec=H.HISQ_F32), stream=stream)
+        got = H.hisq_cdot_noalloc(xs, [src[k] for k in range(4)], stream=stream)
+        want = [np.vdot(xs[k].cpu().numpy(), src[k].cpu().numpy()) for k in range(4)]
+        assert np.allclose(got, want, rtol=1e-12)
+    finally:
+        H.hisq_gauge_free(g)
