@@ -826,19 +826,22 @@ def run_batched(args):
     e1.record(stream)
     e1.synchronize()
     t_batched = e0.elapsed_time(e1) / 1e3
-    e0.record(stream)
-    for pr in probs:
+    alone = []
+    for pr in probs:      # each problem alone, one after another
+        e0.record(stream)
         H.hisq_cg_solve(pr["g"], pr["mass"], 0.0, pr["b"], pr["x"], TOL, params, stream=stream)
-    e1.record(stream)
-    e1.synchronize()
-    t_seq = e0.elapsed_time(e1) / 1e3
+        e1.record(stream)
+        e1.synchronize()
+        alone.append(e0.elapsed_time(e1) / 1e3)
+    t_seq = sum(alone)
     nrhs = sum(n for _, n, _ in cases)
-    for tinfo, st, (Ls, n, m) in zip(tuned, stats, cases):
+    for tinfo, st, (Ls, n, m), ta in zip(tuned, stats, cases, alone):
         tinfo.update({"iterations": st.total_iters, "reliable_updates": st.reliable_updates,
-                      "max_true_rel_res": max(st.true_rel_res[k] for k in range(n))})
+                      "max_true_rel_res": max(st.true_rel_res[k] for k in range(n)), "s_alone": ta})
     print(json.dumps({"workload": "batched uneven lattices, FP16 inner", "s_batched": t_batched,
-                      "s_sequential": t_seq, "s_per_rhs_batched": t_batched / nrhs, "nrhs": nrhs,
-                      "problems": tuned}), flush=True)
+                      "s_sequential": t_seq, "s_longest_alone": max(alone),
+                      "batched_over_longest_alone": t_batched / max(alone),
+                      "s_per_rhs_batched": t_batched / nrhs, "nrhs": nrhs, "problems": tuned}), flush=True)
     for g in handles:
         H.hisq_gauge_free(g)
 

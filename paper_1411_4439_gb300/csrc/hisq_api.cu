@@ -479,6 +479,8 @@ int kind_of_flags(int flags) {
 }
 
 int bundle_kind_of_flags(int flags) {
+    if ((flags & HISQ_MAP_STAGED) && (flags & HISQ_MAP_COMPACT))
+        return (flags & HISQ_MAP_PIPELINED2) ? KIND_BUNDLE_CSMEM3 : KIND_BUNDLE_CSMEM1;
     if (flags & HISQ_MAP_STAGED) return (flags & HISQ_MAP_PIPELINED2) ? KIND_BUNDLE_SMEM2 : KIND_BUNDLE_SMEM1;
     const bool spin = flags & (HISQ_MAP_PIPELINED | HISQ_MAP_PIPELINED2);
     if (flags & HISQ_MAP_COMPACT) return spin ? KIND_BUNDLE_COMPACT_SPIN : KIND_BUNDLE_COMPACT;
@@ -488,6 +490,8 @@ int bundle_kind_of_flags(int flags) {
 int flags_of_tune(const DslashTune& t) {
     if (t.layout == HISQ_BUNDLE && (t.kind == KIND_BUNDLE_SMEM1 || t.kind == KIND_BUNDLE_SMEM2))
         return HISQ_MAP_STAGED | (t.kind == KIND_BUNDLE_SMEM2 ? HISQ_MAP_PIPELINED2 : 0);
+    if (t.layout == HISQ_BUNDLE && (t.kind == KIND_BUNDLE_CSMEM1 || t.kind == KIND_BUNDLE_CSMEM3))
+        return HISQ_MAP_STAGED | HISQ_MAP_COMPACT | (t.kind == KIND_BUNDLE_CSMEM3 ? HISQ_MAP_PIPELINED2 : 0);
     if (t.layout == HISQ_BUNDLE)
         return (t.kind == KIND_BUNDLE_COMPACT || t.kind == KIND_BUNDLE_COMPACT_SPIN ? HISQ_MAP_COMPACT : 0) |
                (t.kind == KIND_BUNDLE_SPIN || t.kind == KIND_BUNDLE_COMPACT_SPIN ? HISQ_MAP_PIPELINED : 0);
@@ -514,8 +518,9 @@ DslashTune pick_tune(hisq_gauge g, int n, int prec, int requested, int layout) {
         const int ru = link_recon_u(g, prec), rn = link_recon_n(g, prec);
         const int r = requested ? requested : g->tune_rpt;
         if (r && n % r == 0 && n / r <= 4) {
-            const int b = (!requested && g->tune_minb) ? g->tune_minb : (r == 8 ? 3 : 4);
-            const int k = requested ? KIND_BUNDLE : bundle_kind_of_flags(g->tune_flags);
+            const int b = (!requested && g->tune_minb) ? g->tune_minb : (r == 8 && prec != HISQ_F16 ? 3 : 4);
+            const int k = requested ? (r == 8 && prec == HISQ_F16 ? KIND_BUNDLE_CSMEM1 : KIND_BUNDLE)
+                                    : bundle_kind_of_flags(g->tune_flags);
             if (bundle_mapping_built(prec, ru, rn, r, b, k)) {
                 t.rpt = r;
                 t.minb = b;
@@ -756,7 +761,7 @@ std::vector<DslashTune> candidate_tunes(hisq_gauge g, int n, int prec, int layou
     if (layout == HISQ_BUNDLE) {
         const int ru = link_recon_u(g, prec), rn = link_recon_n(g, prec);
         const int kinds[] = {KIND_BUNDLE, KIND_BUNDLE_SPIN, KIND_BUNDLE_COMPACT, KIND_BUNDLE_COMPACT_SPIN,
-                             KIND_BUNDLE_SMEM1, KIND_BUNDLE_SMEM2};
+                             KIND_BUNDLE_SMEM1, KIND_BUNDLE_SMEM2, KIND_BUNDLE_CSMEM1, KIND_BUNDLE_CSMEM3};
         for (int r : {4, 8}) {
             if (n % r != 0 || n / r > 4) continue;
             for (int b = 1; b <= 4; ++b)

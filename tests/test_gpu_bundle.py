@@ -140,7 +140,8 @@ def test_bundle_dslash_matches_oracle(gpu_lib, L, prec, ru, rn):
 MAPPINGS = [(8, 3, 0), (4, 4, 0), (8, 3, 128), (8, 2, 0), (4, 3, 0), (4, 4, 128),
             (8, 1, 0), (8, 1, 8), (8, 2, 8), (4, 3, 8),
             (8, 2, 128), (8, 4, 128), (4, 3, 128), (8, 2, 136), (8, 3, 136), (4, 3, 136), (4, 4, 136),
-            (8, 2, 4), (8, 3, 4), (8, 4, 4), (8, 2, 4 | 16), (8, 3, 4 | 16), (4, 4, 4)]
+            (8, 2, 4), (8, 3, 4), (8, 4, 4), (8, 2, 4 | 16), (8, 3, 4 | 16), (4, 4, 4),
+            (8, 3, 4 | 128), (8, 4, 4 | 128), (8, 3, 4 | 128 | 16), (8, 4, 4 | 128 | 16), (4, 4, 4 | 128 | 16)]
 
 
 @pytest.mark.parametrize("prec", [1, 2])
