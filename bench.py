@@ -179,7 +179,12 @@ class ClockSampler:
 # DRAM bytes (read + write) of one launch of a roofline Dslash, from one ncu
 # capture of that kernel (profiles/), keyed by (precision, lattice, n, rhs per
 # thread, min blocks, mapping flags). A mapping without a capture reports null.
-DSLASH_TRAFFIC = {}
+DSLASH_TRAFFIC = {
+    # profiles/dslash_bundle_f16_r18_r14_n8_48x48x48x12.md: 418.9 MB read + 37.1 MB written
+    ("f16", (48, 48, 48, 12), 8, 8, 4, 132): 455975424,
+    # profiles/dslash_bundle_f32_r18_r14_n8_48x48x48x12.md: 831.5 MB read + 100.1 MB written
+    ("f32", (48, 48, 48, 12), 8, 8, 3, 0): 931567104,
+}
 
 
 def measured_peaks() -> dict:
@@ -361,7 +366,8 @@ def run_gpu(args):
     dslash_info = {"f16": {"us_per_launch": round(t_d * 1e6, 2), "gbs": round(gbs, 1),
                            "frac_of_8tbs": round(gbs / NOMINAL_HBM_GBS, 4), "hbm_frac": hbm["frac"],
                            "tflops": round(tfl, 2), "alu_frac": alu["frac"],
-                           "flop_per_byte": round(intensity, 2), "mapping": list(mapping)}}
+                           "flop_per_byte": round(intensity, 2), "mapping": list(mapping),
+                           "traffic": traffic_d}}
     g32 = H.hisq_gauge_load(L, dU, dN, prec=H.HISQ_F32, recon_U=18, recon_N=14)
     t32, b32, f32 = time_bundle_dslash(H, torch, g32, H.HISQ_F32, NRHS, stream, flush)
     dslash_info["f32"] = {"us_per_launch": round(t32 * 1e6, 2), "gbs": round(b32 / t32 / 1e9, 1),
@@ -371,6 +377,7 @@ def run_gpu(args):
                           "flop_per_byte": round(f32 / b32, 2),
                           "mapping": list(H.hisq_get_dslash_mapping_ex(g32, NRHS, H.HISQ_F32,
                                                                                  H.HISQ_BUNDLE))}
+    dslash_info["f32"]["traffic"] = dslash_traffic("f32", L, NRHS, dslash_info["f32"]["mapping"])
     H.hisq_gauge_free(g32)
 
     # ---- end to end through the C ABI with pinned host buffers ----
@@ -787,7 +794,7 @@ def run_dslash_sweep(args):
 
 def run_batched(args):
     """Three gauge fields of uneven volume solved by one hisq_cg_solve_batched
-    call (one CUDA graph per chunk of iterations): 24^3x6 with n = 16
+    call (one CUDA graph holding a device-driven loop per problem): 24^3x6 with n = 16
     (m = 0.002), 32^3x8 with n = 8 (m = 0.01), 64^3x16 with n = 4 (m = 0.01);
     FP16 storage with FP32 arithmetic and FP64 reliable updates, Z2 sources,
     link compression and thread mapping chosen by the autotuner. Also times
@@ -811,7 +818,7 @@ def run_batched(args):
         handles.append(g)
         bundle = H.hisq_autotune_bundle(g, n, H.HISQ_F16)
         tuned.append({"lattice": list(Ls), "n": n, "mass": m, "recon": [g.recon_U, g.recon_N],
-                      "mapping": list(H.hisq_get_dslash_mapping(g, n, H.HISQ_F16)),
+                      "mapping": list(H.hisq_get_dslash_mapping_ex(g, n, H.HISQ_F16, H.HISQ_BUNDLE)),
                       "bundle_tuner_best_n": bundle["n"]})
         b = gen.z2_source(Ls, n, seed=SOURCE_SEED + i)
         bt = [torch.from_numpy(b[k]).to(dev) for k in range(n)]
@@ -987,7 +994,8 @@ def run_cg_probe(args):
     b = gen.gaussian_source(Ls, args.n, seed=SOURCE_SEED)
     bt = [torch.from_numpy(b[k]).to(dev) for k in range(args.n)]
     xt = [torch.zeros_like(t) for t in bt]
-    p = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=RELIABLE_EVERY, maxiter=args.maxiter)
+    p = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=RELIABLE_EVERY, maxiter=args.maxiter,
+                    device_loop=args.device_loop)
     for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1026,6 +1034,8 @@ def main(argv=None):
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--op", choices=["dslash", "mdagm"], default="dslash")
     ap.add_argument("--maxiter", type=int, default=400, help="cg-probe: iteration cap")
+    ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
+                    help="cg-probe: 1 = the whole solve as one graph launch, 0 = one launch per kernel")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -800,9 +800,10 @@ __global__ void __launch_bounds__(128, MINB) dslash_bundle_kernel(const DslashAr
         red0[j] = 0.f;
         red1[j] = 0.f;
     }
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h - (int)threadIdx.x < vh;
-         h += gridDim.x * blockDim.x) {
-        if (h >= vh) continue;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v - (int)threadIdx.x < vh;
+         v += gridDim.x * blockDim.x) {
+        if (v >= vh) continue;
+        const int h = visit_site(v, a.g);
         if constexpr (EPI == EPI_X) {
             // the epilogue's x is read after the hops; start it towards L2 now
             const uint4* xb = reinterpret_cast<const uint4*>(a.x[0]) + gofs + h;

@@ -213,9 +213,10 @@ __global__ void __launch_bounds__(256, MINB) dslash_pipe_kernel(const DslashArgs
         red0[j] = (R)0;
         red1[j] = (R)0;
     }
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h - (int)threadIdx.x < vh;
-         h += gridDim.x * blockDim.x) {
-        if (h >= vh) continue;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v - (int)threadIdx.x < vh;
+         v += gridDim.x * blockDim.x) {
+        if (v >= vh) continue;
+        const int h = visit_site(v, a.g);
         RC acc[RPT][3];
 #pragma unroll
         for (int j = 0; j < RPT; ++j)

@@ -259,3 +259,35 @@ def test_bundle_cg_matches_oracle(gpu_lib, prec, ru, rn, mass):
         assert st.total_iters > 0
     finally:
         H.hisq_gauge_free(g)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("rpt,minb,flags", [(8, 3, 0), (8, 3, 4), (8, 4, 4 | 128), (8, 3, 4 | 128 | 16),
+                                            (4, 4, 0)])
+def test_bundle_cg_with_a_forced_mapping(gpu_lib, prec, rpt, minb, flags):
+    """The CG's second Dslash carries the x epilogue and Re<x, out> (the CG on
+    A = 4m^2 - D_eo D_oe): the epilogue of every kernel kind against the
+    oracle's solve."""
+    import torch
+    H = gpu_lib
+    L = (4, 6, 8, 10)
+    mass = 0.05
+    U, N = links(L)
+    g = load(H, L, prec, 18, 14)
+    try:
+        H.hisq_set_dslash_mapping(g, rpt, minb, flags)
+        assert H.hisq_get_dslash_mapping_ex(g, 8, prec, H.HISQ_BUNDLE) == (rpt, minb, flags)
+        n = 8
+        b = gen.z2_source(L, n, seed=251)
+        bt = [torch.from_numpy(b[k]).cuda() for k in range(n)]
+        xt = [torch.empty_like(t) for t in bt]
+        p = H.cg_params(inner_prec=prec, spinor_layout=H.HISQ_BUNDLE)
+        H.hisq_cg_solve(g, mass, 0.0, bt, xt, 1e-10, p)
+        x = np.stack([t.cpu().numpy() for t in xt])
+        A = lambda q: O.apply_Ae(U, N, q, L, mass)
+        assert np.all(O.true_relative_residual(A, x, b) <= 1e-10)
+        x_ref, _ = O.cg(A, b, tol=1e-13)
+        for k in range(n):
+            assert rel_l2(x[k], x_ref[k]) <= 1e-8, k
+    finally:
+        H.hisq_gauge_free(g)
