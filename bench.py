@@ -379,6 +379,7 @@ def run_gpu(args):
                                                                                  H.HISQ_BUNDLE))}
     dslash_info["f32"]["traffic"] = dslash_traffic("f32", L, NRHS, dslash_info["f32"]["mapping"])
     H.hisq_gauge_free(g32)
+    cg_kernels = time_cg_kernels(H, torch, g, bt, params, stream)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     hb = [torch.from_numpy(b[k]).pin_memory() for k in range(NRHS)]
@@ -436,6 +437,7 @@ def run_gpu(args):
                          bytes_per_launch=bytes_d, flops_per_launch=flops_d, hbm=hbm, alu=alu,
                          ridge_flop_per_byte=round(ridge, 2)),
         "dslash": dslash_info,
+        "cg_kernels": cg_kernels,
         "link_pack_s": pack_s,
         "fp64": fp64,
         "configs1": configs1,
@@ -455,6 +457,37 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def time_cg_kernels(H, torch, g, bt, params, stream, iters: int = 400) -> dict:
+    """The four launches of a CG iteration of the headline solve, timed hot
+    with CUDA events on the solve's stream (hisq_cg_params.profile_kernels)
+    over the first `iters` iterations, against their byte minima: per site,
+    FP16 spinors of 8 rhs are 96 B and the FP32 solution increment 192 B."""
+    vh = int(np.prod(L)) // 2
+    sp = 12 * NRHS            # FP16 spinor bytes per site
+    xl = 24 * NRHS            # FP32 x_lo bytes per site
+    links = 8 * (18 + 14) * 2
+    minima = {"dslash_t": (links + 2 * sp) * vh,            # t = D_oe p
+              "dslash_ap_alpha": (links + 3 * sp) * vh,     # Ap = 4m^2 p - D_eo t (reads p), Re<p, Ap>
+              "update_r": 3 * sp * vh,                      # r, Ap in; r out
+              "update_px": (3 * sp + 2 * xl) * vh}          # p, x_lo, r in; x_lo, p out
+    p = H.cg_params(inner_prec=params.inner_prec, reliable_every=params.reliable_every,
+                    spinor_layout=params.spinor_layout, maxiter=iters, profile_kernels=1)
+    x = [torch.zeros_like(t) for t in bt]
+    try:
+        st = H.hisq_cg_solve(g, MASS, 0.0, bt, x, TOL, p, stream=stream)
+    except H.HisqError as e:     # HISQ_ENOCONV at the cap: the stats ride on the error
+        st = e.stats
+    peak = measured_peaks()["hbm_gbs"]
+    out = {"iterations_timed": st.profiled_iters}
+    for k, name in enumerate(minima):
+        us = st.kernel_us[k]
+        gbs = minima[name] / (us * 1e-6) / 1e9 if us > 0 else None
+        out[name] = {"us": round(us, 2), "min_bytes": minima[name],
+                     "gbs": None if gbs is None else round(gbs, 1),
+                     "hbm_frac": None if gbs is None else round(gbs / peak, 4)}
+    return out
 
 
 def run_configs1(H, torch, gen, dev, stream) -> dict:
@@ -841,6 +874,14 @@ def run_batched(args):
         e1.synchronize()
         alone.append(e0.elapsed_time(e1) / 1e3)
     t_seq = sum(alone)
+    # the two smaller problems batched without the largest: do they overlap
+    # each other where the largest leaves no room?
+    small = sorted(range(len(probs)), key=lambda i: alone[i])[:2]
+    e0.record(stream)
+    H.hisq_cg_solve_batched([probs[i] for i in small], params, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    t_small_pair = e0.elapsed_time(e1) / 1e3
     nrhs = sum(n for _, n, _ in cases)
     for tinfo, st, (Ls, n, m), ta in zip(tuned, stats, cases, alone):
         tinfo.update({"iterations": st.total_iters, "reliable_updates": st.reliable_updates,
@@ -848,6 +889,8 @@ def run_batched(args):
     print(json.dumps({"workload": "batched uneven lattices, FP16 inner", "s_batched": t_batched,
                       "s_sequential": t_seq, "s_longest_alone": max(alone),
                       "batched_over_longest_alone": t_batched / max(alone),
+                      "s_batched_two_smaller": t_small_pair,
+                      "s_two_smaller_alone": [alone[i] for i in small],
                       "s_per_rhs_batched": t_batched / nrhs, "nrhs": nrhs, "problems": tuned}), flush=True)
     for g in handles:
         H.hisq_gauge_free(g)
@@ -994,8 +1037,8 @@ def run_cg_probe(args):
     b = gen.gaussian_source(Ls, args.n, seed=SOURCE_SEED)
     bt = [torch.from_numpy(b[k]).to(dev) for k in range(args.n)]
     xt = [torch.zeros_like(t) for t in bt]
-    p = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=RELIABLE_EVERY, maxiter=args.maxiter,
-                    device_loop=args.device_loop)
+    p = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=args.reliable_every or RELIABLE_EVERY,
+                    maxiter=args.maxiter, device_loop=args.device_loop)
     for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1004,8 +1047,11 @@ def run_cg_probe(args):
         except H.HisqError as e:      # HISQ_ENOCONV at the cap: the stats ride on the error
             st = e.stats
         torch.cuda.synchronize()
-        print(json.dumps({"workload": "cg probe", "lattice": list(Ls), "n": args.n, "iterations": st.total_iters,
-                          "reliable_updates": st.reliable_updates, "s": time.perf_counter() - t0}), flush=True)
+        print(json.dumps({"workload": "cg probe", "lattice": list(Ls), "n": args.n,
+                          "reliable_every": p.reliable_every, "iterations": st.total_iters,
+                          "reliable_updates": st.reliable_updates,
+                          "max_true_rel_res": max(st.true_rel_res[k] for k in range(args.n)),
+                          "s": time.perf_counter() - t0}), flush=True)
     H.hisq_gauge_free(g)
 
 
@@ -1034,6 +1080,8 @@ def main(argv=None):
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--op", choices=["dslash", "mdagm"], default="dslash")
     ap.add_argument("--maxiter", type=int, default=400, help="cg-probe: iteration cap")
+    ap.add_argument("--reliable-every", type=int, default=0,
+                    help="cg-probe: FP64 reliable update every K iterations (0: the headline's)")
     ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
                     help="cg-probe: 1 = the whole solve as one graph launch, 0 = one launch per kernel")
     args = ap.parse_args(argv)

@@ -382,6 +382,12 @@ typedef struct {
                               reliable_every multiples of check_every; else
                               the host decides after every check_every
                               iterations) (1) */
+    int profile_kernels;   /* 1: time the four launches of every iteration
+                              with CUDA events on the solve's stream and
+                              report their mean durations in
+                              hisq_cg_stats.kernel_us; the solve then launches
+                              every kernel from the host (no graphs, no device
+                              loop), which costs launch overhead (0) */
 } hisq_cg_params;
 
 typedef struct {
@@ -390,6 +396,12 @@ typedef struct {
     int reliable_updates;      /* FP64 residual recomputations */
     double true_rel_res[16];   /* final ||b - A x|| / ||b|| in FP64 per rhs */
     double seconds;            /* wall time of the solve, host clock */
+    int profiled_iters;        /* iterations timed by profile_kernels (0 if off) */
+    double kernel_us[4];       /* with profile_kernels: mean device time (us) per
+                                  iteration of [0] t = D_oe p (both Dslash of the
+                                  full-lattice operator y = M p), [1] Ap and the
+                                  reduction forming alpha, [2] r -= alpha Ap with
+                                  |r|^2 and beta, [3] x += alpha p, p = r + beta p */
 } hisq_cg_stats;
 
 void hisq_cg_default_params(hisq_cg_params* p);

@@ -115,7 +115,7 @@ __device__ bool group_reduce_arrive(const RedScratch& red, float (&val)[NV], int
 
 // r -= alpha Ap (moving rhs) ; rr' = |r|^2 of the stored r ; finish: beta.
 template <typename S>
-__global__ void __launch_bounds__(kThreads) update_r_b_kernel(BlasArgs a, uint4* r, const uint4* Ap) {
+__global__ void __launch_bounds__(kThreads, 4) update_r_b_kernel(BlasArgs a, uint4* r, const uint4* Ap) {
     constexpr int W = Chunk<S>::W;
     const int g = blockIdx.y;
     const long long nch = a.len;   // chunks per group: 3 V_h
@@ -131,21 +131,37 @@ __global__ void __launch_bounds__(kThreads) update_r_b_kernel(BlasArgs a, uint4*
         any = any || mv[l];
     }
     if (any) {
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nch;
-             i += (long long)gridDim.x * blockDim.x) {
-            float2 rv[W], av[W];
-            Chunk<S>::get(__ldg(r + off + i), rv);
-            Chunk<S>::get(__ldg(Ap + off + i), av);
+        // U chunks per thread and pass, all loads issued before the first use
+        constexpr int U = 4;
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < nch; i0 += U * stride) {
+            uint4 rc[U], ac[U];
 #pragma unroll
-            for (int l = 0; l < W; ++l) {
-                if (!mv[l]) continue;   // a resting rhs keeps its residual
-                rv[l].x = fmaf(-alpha[l], av[l].x, rv[l].x);
-                rv[l].y = fmaf(-alpha[l], av[l].y, rv[l].y);
+            for (int u = 0; u < U; ++u) {
+                const long long i = i0 + u * stride;
+                if (i < nch) {
+                    rc[u] = __ldg(r + off + i);
+                    ac[u] = __ldg(Ap + off + i);
+                }
             }
-            r[off + i] = Chunk<S>::put(rv);
-            Chunk<S>::round(rv);   // the norm is that of the stored residual
 #pragma unroll
-            for (int l = 0; l < W; ++l) val[l] = fmaf(rv[l].x, rv[l].x, fmaf(rv[l].y, rv[l].y, val[l]));
+            for (int u = 0; u < U; ++u) {
+                const long long i = i0 + u * stride;
+                if (i >= nch) break;
+                float2 rv[W], av[W];
+                Chunk<S>::get(rc[u], rv);
+                Chunk<S>::get(ac[u], av);
+#pragma unroll
+                for (int l = 0; l < W; ++l) {
+                    if (!mv[l]) continue;   // a resting rhs keeps its residual
+                    rv[l].x = fmaf(-alpha[l], av[l].x, rv[l].x);
+                    rv[l].y = fmaf(-alpha[l], av[l].y, rv[l].y);
+                }
+                r[off + i] = Chunk<S>::put(rv);
+                Chunk<S>::round(rv);   // the norm is that of the stored residual
+#pragma unroll
+                for (int l = 0; l < W; ++l) val[l] = fmaf(rv[l].x, rv[l].x, fmaf(rv[l].y, rv[l].y, val[l]));
+            }
         }
     }
     __shared__ double s_vals[kMaxRedVals];
@@ -337,9 +353,10 @@ __global__ void __launch_bounds__(kThreads) unpack_b_kernel(const uint4* src, co
     }
 }
 
-dim3 bundle_grid(long long chunks, int groups) {
+// At most per_sm blocks per SM over all groups, one chunk per thread.
+dim3 bundle_grid(long long chunks, int groups, int per_sm = 8) {
     long long b = (chunks + kThreads - 1) / kThreads;
-    long long cap = (8ll * device_sm_count() + groups - 1) / groups;
+    long long cap = ((long long)per_sm * device_sm_count() + groups - 1) / groups;
     if (cap < 1) cap = 1;
     if (b > cap) b = cap;
     if (b > kMaxRedBlocks) b = kMaxRedBlocks;
@@ -362,7 +379,8 @@ int bundle_width(int prec) { return prec == HISQ_F32 ? 2 : prec == HISQ_F16 ? 4 
 cudaError_t launch_cg_update_r_bundle(const BlasArgs& a, int prec, void* r, const void* Ap, cudaStream_t s) {
     const int W = bundle_width(prec);
     if (W == 0 || a.n % W) return cudaErrorInvalidValue;
-    HISQ_BUNDLE_SWITCH(prec, (update_r_b_kernel<S><<<bundle_grid(a.len, a.n / W), kThreads, 0, s>>>(
+    // one wave of 4 blocks per SM (64 registers a thread), four chunks a pass
+    HISQ_BUNDLE_SWITCH(prec, (update_r_b_kernel<S><<<bundle_grid(a.len, a.n / W, 4), kThreads, 0, s>>>(
                                  a, (uint4*)r, (const uint4*)Ap)));
     return cudaGetLastError();
 }

@@ -149,6 +149,9 @@ struct Workspace {
     cudaStream_t cap_if = nullptr;     // captures its reliable-update branch
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<std::tuple<int, double, double, int, int, int, double, double>, cudaGraphExec_t> loops;
+    std::vector<cudaEvent_t> prof_ev;  // profile_kernels: 5 events per iteration of a chunk
+    double prof_us[4] = {0, 0, 0, 0};  // summed kernel times of the profiled iterations
+    int prof_iters = 0;
     size_t bytes = 0;
 };
 
@@ -164,6 +167,7 @@ void free_workspace(Workspace* w) {
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
     if (w->cap_body) cudaStreamDestroy(w->cap_body);
     if (w->cap_if) cudaStreamDestroy(w->cap_if);
+    for (cudaEvent_t e : w->prof_ev) cudaEventDestroy(e);
     delete w;
 }
 
@@ -1101,6 +1105,7 @@ extern "C" void hisq_cg_default_params(hisq_cg_params* p) {
     // the bundle layout where n fits it (F32 / F16 even-odd solves), else AoS
     p->spinor_layout = HISQ_BUNDLE;
     p->device_loop = 1;
+    p->profile_kernels = 0;
 }
 
 namespace {
@@ -1252,6 +1257,7 @@ struct Solver {
     Workspace* w;
     int n, prec, full;
     bool bundle = false;       // low-precision vectors in the bundle layout
+    bool profile = false;      // time the launches of each iteration (profile_kernels)
     DslashTune tune, tune64;   // inner (low precision) and FP64 Dslash mappings
     double mass, mu;
     double tol2;
@@ -1291,8 +1297,9 @@ struct Solver {
         return a;
     }
 
-    // Low-precision A p -> Ap; the last reduction block forms alpha.
-    cudaError_t apply_lo(cudaStream_t s) const {
+    // Low-precision A p -> Ap; the last reduction block forms alpha. `mid`
+    // (profiling) is recorded between the first and the second operator half.
+    cudaError_t apply_lo(cudaStream_t s, cudaEvent_t mid = nullptr) const {
         const int ru = g->recon_U, rn = g->recon_N;
         cudaError_t e;
         if (bundle) {
@@ -1300,6 +1307,7 @@ struct Solver {
             a.in[0] = w->p_lo;
             a.out[0] = w->t_lo;
             e = launch_dslash(a, prec, ru, rn, EPI_NONE, tune, s);
+            if (e == cudaSuccess && mid) e = cudaEventRecord(mid, s);
             if (e != cudaSuccess) return e;
             DslashArgs b = args(0, prec);   // Ap = 4m^2 p - D_eo t, pAp = Re<p, Ap>
             b.cx = 4.0 * mass * mass;
@@ -1318,6 +1326,7 @@ struct Solver {
                 a.out[k] = lo_ptr(w->t_lo, k);
             }
             e = launch_dslash(a, prec, ru, rn, EPI_NONE, tune, s);
+            if (e == cudaSuccess && mid) e = cudaEventRecord(mid, s);
             if (e != cudaSuccess) return e;
             DslashArgs b = args(0, prec);   // Ap = 4m^2 p - D_eo t, pAp = Re<p, Ap>
             b.cx = 4.0 * mass * mass;
@@ -1346,6 +1355,10 @@ struct Solver {
             e = launch_dslash(a, prec, ru, rn, EPI_X, tune, s);
             if (e != cudaSuccess) return e;
         }
+        if (mid) {
+            e = cudaEventRecord(mid, s);
+            if (e != cudaSuccess) return e;
+        }
         for (int par = 0; par < 2; ++par) {
             DslashArgs a = args(par, prec);
             set_mu(a, -mu);
@@ -1362,16 +1375,22 @@ struct Solver {
         return launch_dot_alpha(blas(), prec, w->p_lo, w->Ap_lo, s);
     }
 
-    // One CG iteration on every active rhs.
-    cudaError_t iterate(cudaStream_t s) const {
-        cudaError_t e = apply_lo(s);
+    // One CG iteration on every active rhs; ev (profiling) gets 5 events
+    // around its four launches.
+    cudaError_t iterate(cudaStream_t s, const cudaEvent_t* ev = nullptr) const {
+        cudaError_t e = ev ? cudaEventRecord(ev[0], s) : cudaSuccess;
+        if (e == cudaSuccess) e = apply_lo(s, ev ? ev[1] : nullptr);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
         if (bundle) {
             if (e == cudaSuccess) e = launch_cg_update_r_bundle(blas(), prec, w->r_lo, w->Ap_lo, s);
+            if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
             if (e == cudaSuccess) e = launch_cg_update_px_bundle(blas(), prec, w->x_lo, w->r_lo, w->p_lo, s);
-            return e;
+        } else {
+            if (e == cudaSuccess) e = launch_cg_update_r(blas(), prec, w->r_lo, w->Ap_lo, s);
+            if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+            if (e == cudaSuccess) e = launch_cg_update_px(blas(), prec, w->x_lo, w->r_lo, w->p_lo, s);
         }
-        if (e == cudaSuccess) e = launch_cg_update_r(blas(), prec, w->r_lo, w->Ap_lo, s);
-        if (e == cudaSuccess) e = launch_cg_update_px(blas(), prec, w->x_lo, w->r_lo, w->p_lo, s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], s);
         return e;
     }
 
@@ -1525,6 +1544,29 @@ struct Solver {
 
     // Run `chunk` iterations, from a captured graph when enabled.
     hisq_status run_chunk(int chunk, bool graphs, cudaStream_t s) {
+        if (profile) {
+            // every iteration but the chunk's first (which follows the host's
+            // poll, so the GPU may wait for its launch) is timed
+            const size_t need = 5 * (size_t)chunk;
+            while (w->prof_ev.size() < need) {
+                cudaEvent_t e;
+                HISQ_CUDA(cudaEventCreate(&e));
+                w->prof_ev.push_back(e);
+            }
+            for (int i = 0; i < chunk; ++i) HISQ_CUDA(iterate(s, i > 0 ? &w->prof_ev[5 * i] : nullptr));
+            if (chunk > 1) {
+                HISQ_CUDA(cudaEventSynchronize(w->prof_ev[5 * (chunk - 1) + 4]));
+                for (int i = 1; i < chunk; ++i) {
+                    for (int k = 0; k < 4; ++k) {
+                        float ms = 0.f;
+                        HISQ_CUDA(cudaEventElapsedTime(&ms, w->prof_ev[5 * i + k], w->prof_ev[5 * i + k + 1]));
+                        w->prof_us[k] += 1e3 * ms;
+                    }
+                    ++w->prof_iters;
+                }
+            }
+            return HISQ_OK;
+        }
         if (!graphs) {
             for (int i = 0; i < chunk; ++i) HISQ_CUDA(iterate(s));
             return HISQ_OK;
@@ -1610,6 +1652,10 @@ struct CgRun {
             return fail(HISQ_EINVAL, "unknown spinor layout %d", prm.spinor_layout);
         if (!(prm.reliable_delta >= 0.0 && prm.reliable_delta < 1.0))
             return fail(HISQ_EINVAL, "reliable_delta must be in [0, 1)");
+        if (prm.profile_kernels) {   // the timed launches come from the host
+            prm.use_graphs = 0;
+            prm.device_loop = 0;
+        }
         *out = prm;
         return HISQ_OK;
     }
@@ -1640,6 +1686,9 @@ struct CgRun {
         sv.mass = mass;
         sv.mu = mu;
         sv.tol2 = tol * tol;
+        sv.profile = prm.profile_kernels != 0;
+        for (int k = 0; k < 4; ++k) w->prof_us[k] = 0.0;
+        w->prof_iters = 0;
         for (int k = 0; k < n; ++k) iters_k[k] = seen_restarts[k] = bad_updates[k] = 0;
 
         // sources and initial guess into the FP64 blocks; the caller's vectors
@@ -1844,6 +1893,9 @@ struct CgRun {
             }
             stats->total_iters = iter;
             stats->reliable_updates = reliable;
+            stats->profiled_iters = w->prof_iters;
+            for (int k = 0; k < 4; ++k)
+                stats->kernel_us[k] = w->prof_iters > 0 ? w->prof_us[k] / w->prof_iters : 0.0;
             stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         }
         return res;

@@ -64,13 +64,14 @@ class hisq_cg_params(ctypes.Structure):
                 ("use_x0", ctypes.c_int), ("even_odd", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("rhs_per_thread", ctypes.c_int), ("spinor_layout", ctypes.c_int),
-                ("device_loop", ctypes.c_int)]
+                ("device_loop", ctypes.c_int), ("profile_kernels", ctypes.c_int)]
 
 
 class hisq_cg_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * MAX_RHS), ("total_iters", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int),
-                ("true_rel_res", ctypes.c_double * MAX_RHS), ("seconds", ctypes.c_double)]
+                ("true_rel_res", ctypes.c_double * MAX_RHS), ("seconds", ctypes.c_double),
+                ("profiled_iters", ctypes.c_int), ("kernel_us", ctypes.c_double * 4)]
 
 
 class hisq_cg_problem(ctypes.Structure):

@@ -122,3 +122,33 @@ def test_new_entry_points_reject_bad_arguments_before_cuda(lib):
     err = lib.hisq_last_error
     err.restype = ctypes.c_char_p
     assert b"NULL handle" in err()
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structures have the size and field offsets a C compiler
+    gives the header's structures (compiled here with the host compiler)."""
+    import shutil
+    import subprocess
+
+    from paper_1411_4439_gb300 import hisq as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"hisq_cg_params": B.hisq_cg_params, "hisq_cg_stats": B.hisq_cg_stats,
+               "hisq_cg_problem": B.hisq_cg_problem}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "hisq.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)

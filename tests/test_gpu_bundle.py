@@ -291,3 +291,30 @@ def test_bundle_cg_with_a_forced_mapping(gpu_lib, prec, rpt, minb, flags):
             assert rel_l2(x[k], x_ref[k]) <= 1e-8, k
     finally:
         H.hisq_gauge_free(g)
+
+
+def test_profiled_solve_times_every_launch_and_still_converges(gpu_lib):
+    """profile_kernels runs the iterations from the host with CUDA events
+    around the four launches; the solve itself is unchanged."""
+    import torch
+    H = gpu_lib
+    L = (4, 6, 8, 10)
+    mass = 0.05
+    U, N = links(L)
+    g = load(H, L, 2, 18, 14)
+    try:
+        n = 8
+        b = gen.z2_source(L, n, seed=252)
+        bt = [torch.from_numpy(b[k]).cuda() for k in range(n)]
+        xt = [torch.empty_like(t) for t in bt]
+        p = H.cg_params(inner_prec=2, spinor_layout=H.HISQ_BUNDLE, profile_kernels=1)
+        st = H.hisq_cg_solve(g, mass, 0.0, bt, xt, 1e-10, p)
+        assert 0 < st.profiled_iters < st.total_iters
+        assert all(st.kernel_us[k] > 0 for k in range(4))
+        x = np.stack([t.cpu().numpy() for t in xt])
+        A = lambda q: O.apply_Ae(U, N, q, L, mass)
+        assert np.all(O.true_relative_residual(A, x, b) <= 1e-10)
+        st0 = H.hisq_cg_solve(g, mass, 0.0, bt, xt, 1e-10, H.cg_params(inner_prec=2, spinor_layout=H.HISQ_BUNDLE))
+        assert st0.profiled_iters == 0 and abs(st0.total_iters - st.total_iters) <= 10
+    finally:
+        H.hisq_gauge_free(g)
