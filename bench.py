@@ -53,7 +53,10 @@ L = (48, 48, 48, 12)
 NRHS = 8
 MASS = 0.0025
 TOL = 1e-10
-RELIABLE_EVERY = 200
+# FP64 reliable update every 150 iterations: at 48^3x12, m = 0.0025 a solve of
+# 8 rhs took 7.76 / 7.59 / 7.50 / 7.57 / 8.61 s at 100 / 125 / 150 / 200 / 300
+# (fewer iterations against more FP64 updates); at 400 it did not converge
+RELIABLE_EVERY = 150
 # the multi-rhs FP32 configuration (reported beside the headline)
 L1 = (32, 32, 32, 8)
 MASS1 = 0.01
@@ -741,7 +744,8 @@ def run_cg_configs(args):
     g = H.hisq_gauge_load(L2, dU, dN, prec=H.HISQ_F16, recon_U=18, recon_N=14)
     bt = dev_list(b)
     xt = [torch.zeros_like(x) for x in bt]
-    t16, st16 = _time_solve(H, torch, g, 0.0025, 0.0, bt, xt, TOL, H.cg_params(inner_prec=H.HISQ_F16), stream)
+    t16, st16 = _time_solve(H, torch, g, 0.0025, 0.0, bt, xt, TOL,
+                            H.cg_params(inner_prec=H.HISQ_F16, reliable_every=RELIABLE_EVERY), stream)
     H.hisq_gauge_free(g)
     g = H.hisq_gauge_load(L2, dU, dN, prec=H.HISQ_F64)
     x64 = [torch.zeros_like(bt[0])]
@@ -771,8 +775,9 @@ def run_cg_configs(args):
 
 def run_dslash_sweep(args):
     """Autotuned Dslash (AoS spinors) for n = 1..16 on 48^3x12 and 64^3x16 in
-    FP64 18/18, FP32 18/14, FP16 18/14 and FP16 12/14: time per launch,
-    algorithmic GB/s and its fraction of the measured HBM peak, GFlop/s."""
+    FP64 18/18, FP32 18/14, FP16 18/14 and FP16 12/14, and on the bundle
+    layout for n = 4, 8, 16: time per launch, algorithmic GB/s and its
+    fraction of the measured HBM peak, GFlop/s."""
     import torch
 
     import hisq_inputs as gen
@@ -820,6 +825,37 @@ def run_dslash_sweep(args):
                                   "mapping": [tune["rhs_per_thread"], tune["min_blocks"], tune["flags"]]}),
                       flush=True)
                 del vs, ws
+            if prec != H.HISQ_F64:
+                # the CG's own layout: rhs-interleaved bundle chunks
+                for n in (4, 8, 16):
+                    src = [torch.randn(vh, 3, dtype=torch.complex128, device=dev) for _ in range(n)]
+                    el = 4 if prec == H.HISQ_F32 else 2
+                    vb = torch.empty(H.hisq.bundle_bytes(g, n, prec) // el,
+                                     dtype=torch.float32 if prec == H.HISQ_F32 else torch.float16, device=dev)
+                    H.hisq_bundle_pack(g, src, prec, vb)
+                    wb = torch.empty_like(vb)
+                    del src
+                    tune = H.hisq_autotune_dslash(g, n, prec, H.HISQ_BUNDLE, 5)
+                    for _ in range(3):
+                        H.hisq_dslash_ex(g, 0.0, vb, wb, 0, prec, H.HISQ_BUNDLE, stream=stream, n=n)
+                    reps = 20
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(reps):
+                        H.hisq_dslash_ex(g, 0.0, vb, wb, 0, prec, H.HISQ_BUNDLE, stream=stream, n=n)
+                    e1.record(stream)
+                    e1.synchronize()
+                    t = e0.elapsed_time(e1) / 1e3 / reps
+                    nb = dslash_bytes_per_site(n, ru, rn, sizes[prec], sizes[prec]) * vh
+                    print(json.dumps({"workload": "dslash sweep", "layout": "bundle", "lattice": list(Ls),
+                                      "prec": names[prec], "recon": [ru, rn], "n": n, "us": round(t * 1e6, 2),
+                                      "alg_gbs": round(nb / t / 1e9, 1),
+                                      "frac_of_measured_hbm": round(nb / t / 1e9 / peak["hbm_gbs"], 4),
+                                      "gflops": round(DSLASH_FLOPS_PER_SITE_RHS * n * vh / t / 1e9, 1),
+                                      "mapping": [tune["rhs_per_thread"], tune["min_blocks"], tune["flags"]]}),
+                          flush=True)
+                    del vb, wb
             H.hisq_gauge_free(g)
         del dU, dN
         torch.cuda.empty_cache()
@@ -1038,7 +1074,7 @@ def run_cg_probe(args):
     bt = [torch.from_numpy(b[k]).to(dev) for k in range(args.n)]
     xt = [torch.zeros_like(t) for t in bt]
     p = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=args.reliable_every or RELIABLE_EVERY,
-                    maxiter=args.maxiter, device_loop=args.device_loop)
+                    maxiter=args.maxiter, device_loop=args.device_loop, x_lo_half=args.x_lo_half)
     for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1048,7 +1084,8 @@ def run_cg_probe(args):
             st = e.stats
         torch.cuda.synchronize()
         print(json.dumps({"workload": "cg probe", "lattice": list(Ls), "n": args.n,
-                          "reliable_every": p.reliable_every, "iterations": st.total_iters,
+                          "reliable_every": p.reliable_every, "x_lo_half": p.x_lo_half,
+                          "iterations": st.total_iters,
                           "reliable_updates": st.reliable_updates,
                           "max_true_rel_res": max(st.true_rel_res[k] for k in range(args.n)),
                           "s": time.perf_counter() - t0}), flush=True)
@@ -1082,6 +1119,8 @@ def main(argv=None):
     ap.add_argument("--maxiter", type=int, default=400, help="cg-probe: iteration cap")
     ap.add_argument("--reliable-every", type=int, default=0,
                     help="cg-probe: FP64 reliable update every K iterations (0: the headline's)")
+    ap.add_argument("--x-lo-half", type=int, choices=[0, 1], default=0,
+                    help="cg-probe: solution increment between reliable updates in half precision")
     ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
                     help="cg-probe: 1 = the whole solve as one graph launch, 0 = one launch per kernel")
     args = ap.parse_args(argv)

@@ -382,6 +382,11 @@ typedef struct {
                               reliable_every multiples of check_every; else
                               the host decides after every check_every
                               iterations) (1) */
+    int x_lo_half;         /* 1: with FP16 inner storage in the bundle layout,
+                              the solution increment gathered between two
+                              reliable updates is stored in half precision
+                              (scaled like the spinors) instead of FP32; x
+                              itself stays FP64 (0) */
     int profile_kernels;   /* 1: time the four launches of every iteration
                               with CUDA events on the solve's stream and
                               report their mean durations in
@@ -425,9 +430,11 @@ void hisq_cg_default_params(hisq_cg_params* p);
  * reliable update recomputes r = b - A x in FP64 with FP64 links and adds
  * the low-precision solution increment into the FP64 x. Convergence is
  * declared per rhs on the FP64 true residual only.
- * Returns HISQ_OK when every rhs reached p->tol, HISQ_ENOCONV at maxiter
- * (x holds the last iterate, stats filled), HISQ_EBREAKDOWN, HISQ_ENAN,
- * HISQ_EINVAL (bad n, tol, pointers or mu != 0 with even_odd).
+ * Returns HISQ_OK when every rhs reached p->tol, HISQ_ENOCONV at maxiter,
+ * HISQ_EBREAKDOWN, HISQ_ENAN (after any of these three, x[k] holds the
+ * solution at the lowest FP64 residual rhs k reached, which is the residual
+ * stats->true_rel_res reports), HISQ_EINVAL (bad n, tol, pointers or mu != 0
+ * with even_odd).
  * Synchronises `stream` before returning.
  */
 hisq_status hisq_cg_solve(hisq_gauge g, double mass, double mu,

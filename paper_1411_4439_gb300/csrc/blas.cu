@@ -506,6 +506,20 @@ cudaError_t launch_norm_bb(const BlasArgs& a, const double2* b, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(kThreads) keep_best_kernel(BlasArgs a, const double2* x, double2* xb) {
+    const int k = blockIdx.y;
+    if (!a.cg->keep[k]) return;
+    const long long off = (long long)k * a.len;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.len;
+         i += (long long)gridDim.x * blockDim.x)
+        xb[off + i] = x[off + i];
+}
+
+cudaError_t launch_keep_best(const BlasArgs& a, const double2* x, double2* x_best, cudaStream_t s) {
+    keep_best_kernel<<<blas_grid(a.len, a.n), kThreads, 0, s>>>(a, x, x_best);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_copy_residual(const BlasArgs& a, const double2* b, double2* r_hi, double tol2,
                                  cudaStream_t s) {
     copy_residual_kernel<<<blas_grid(a.len, a.n), kThreads, 0, s>>>(a, b, r_hi, tol2);

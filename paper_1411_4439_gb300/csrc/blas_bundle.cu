@@ -89,6 +89,25 @@ __device__ __forceinline__ void xlo_put(float* b, long long i, const float2 (&v)
     }
 }
 
+// The solution increment in either storage: FP32 (xlo_get/put above) or,
+// with FP16 inner storage, half chunks laid out like the spinors.
+template <int W, bool XH>
+__device__ __forceinline__ void xinc_get(const void* b, long long i, float2 (&v)[W]) {
+    if constexpr (XH) {
+        static_assert(W == 4, "half increments come with FP16 storage");
+        Chunk<__half>::get(__ldg(reinterpret_cast<const uint4*>(b) + i), v);
+    } else {
+        xlo_get<W>(reinterpret_cast<const float*>(b), i, v);
+    }
+}
+template <int W, bool XH>
+__device__ __forceinline__ void xinc_put(void* b, long long i, const float2 (&v)[W]) {
+    if constexpr (XH)
+        reinterpret_cast<uint4*>(b)[i] = Chunk<__half>::put(v);
+    else
+        xlo_put<W>(reinterpret_cast<float*>(b), i, v);
+}
+
 // Per-rhs sums of a block (NV values per thread, value j of group blockIdx.y
 // is rhs blockIdx.y * NV + j) into the partial slots; in the last block,
 // s_vals[0 .. G * NV) holds the grid sums. Returns true in the last block.
@@ -169,8 +188,8 @@ __global__ void __launch_bounds__(kThreads, 4) update_r_b_kernel(BlasArgs a, uin
 }
 
 // x_lo += alpha p ; p = r + beta p (moving rhs), both from the old p.
-template <typename S>
-__global__ void __launch_bounds__(kThreads) update_px_b_kernel(BlasArgs a, float* x, const uint4* r, uint4* p) {
+template <typename S, bool XH>
+__global__ void __launch_bounds__(kThreads, 4) update_px_b_kernel(BlasArgs a, void* x, const uint4* r, uint4* p) {
     constexpr int W = Chunk<S>::W;
     const int g = blockIdx.y;
     const long long nch = a.len;
@@ -187,39 +206,55 @@ __global__ void __launch_bounds__(kThreads) update_px_b_kernel(BlasArgs a, float
         any_p = any_p || mv[l];
     }
     if (!any_x && !any_p) return;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nch;
-         i += (long long)gridDim.x * blockDim.x) {
-        float2 pv[W];
-        Chunk<S>::get(__ldg(p + off + i), pv);
-        if (any_x) {
-            float2 xv[W];
-            xlo_get<W>(x, (long long)off + i, xv);
+    // U chunks per thread and pass, all loads issued before the first use
+    constexpr int U = 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < nch; i0 += U * stride) {
+        uint4 pc[U], rc[U];
+        float2 xv[U][W];
 #pragma unroll
-            for (int l = 0; l < W; ++l) {
-                if (alpha[l] == 0.f) continue;
-                xv[l].x = fmaf(alpha[l], pv[l].x, xv[l].x);
-                xv[l].y = fmaf(alpha[l], pv[l].y, xv[l].y);
+        for (int u = 0; u < U; ++u) {
+            const long long i = i0 + u * stride;
+            if (i < nch) {
+                pc[u] = __ldg(p + off + i);
+                if (any_x) xinc_get<W, XH>(x, (long long)off + i, xv[u]);
+                if (any_p) rc[u] = __ldg(r + off + i);
             }
-            xlo_put<W>(x, (long long)off + i, xv);
         }
-        if (any_p) {
-            float2 rv[W];
-            Chunk<S>::get(__ldg(r + off + i), rv);
 #pragma unroll
-            for (int l = 0; l < W; ++l) {
-                if (mv[l]) {
-                    pv[l].x = fmaf(beta[l], pv[l].x, rv[l].x);
-                    pv[l].y = fmaf(beta[l], pv[l].y, rv[l].y);
+        for (int u = 0; u < U; ++u) {
+            const long long i = i0 + u * stride;
+            if (i >= nch) break;
+            float2 pv[W];
+            Chunk<S>::get(pc[u], pv);
+            if (any_x) {
+#pragma unroll
+                for (int l = 0; l < W; ++l) {
+                    if (alpha[l] == 0.f) continue;
+                    xv[u][l].x = fmaf(alpha[l], pv[l].x, xv[u][l].x);
+                    xv[u][l].y = fmaf(alpha[l], pv[l].y, xv[u][l].y);
                 }
+                xinc_put<W, XH>(x, (long long)off + i, xv[u]);
             }
-            p[off + i] = Chunk<S>::put(pv);
+            if (any_p) {
+                float2 rv[W];
+                Chunk<S>::get(rc[u], rv);
+#pragma unroll
+                for (int l = 0; l < W; ++l) {
+                    if (mv[l]) {
+                        pv[l].x = fmaf(beta[l], pv[l].x, rv[l].x);
+                        pv[l].y = fmaf(beta[l], pv[l].y, rv[l].y);
+                    }
+                }
+                p[off + i] = Chunk<S>::put(pv);
+            }
         }
     }
 }
 
 // x_hi (FP64, [V_h][3] per rhs) += x_lo / scale ; x_lo = 0 (active rhs).
-template <int W>
-__global__ void __launch_bounds__(kThreads) accum_b_kernel(BlasArgs a, double2* x_hi, float* x_lo, int vh) {
+template <int W, bool XH>
+__global__ void __launch_bounds__(kThreads) accum_b_kernel(BlasArgs a, double2* x_hi, void* x_lo, int vh) {
     const int g = blockIdx.y;
     const long long nch = a.len;
     const size_t off = (size_t)g * nch;
@@ -238,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) accum_b_kernel(BlasArgs a, double2* 
         const int c = (int)(i / vh);
         const long long h = i - (long long)c * vh;
         float2 lo[W];
-        xlo_get<W>(x_lo, (long long)off + i, lo);
+        xinc_get<W, XH>(x_lo, (long long)off + i, lo);
 #pragma unroll
         for (int l = 0; l < W; ++l) {
             if (!act[l]) continue;
@@ -249,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) accum_b_kernel(BlasArgs a, double2* 
             *xp = v;
             lo[l] = make_float2(0.f, 0.f);
         }
-        xlo_put<W>(x_lo, (long long)off + i, lo);
+        xinc_put<W, XH>(x_lo, (long long)off + i, lo);
     }
 }
 
@@ -386,22 +421,30 @@ cudaError_t launch_cg_update_r_bundle(const BlasArgs& a, int prec, void* r, cons
 }
 
 cudaError_t launch_cg_update_px_bundle(const BlasArgs& a, int prec, void* x, const void* r, void* p,
-                                       cudaStream_t s) {
+                                       bool x_half, cudaStream_t s) {
     const int W = bundle_width(prec);
-    if (W == 0 || a.n % W) return cudaErrorInvalidValue;
-    HISQ_BUNDLE_SWITCH(prec, (update_px_b_kernel<S><<<bundle_grid(a.len, a.n / W), kThreads, 0, s>>>(
-                                 a, (float*)x, (const uint4*)r, (uint4*)p)));
+    if (W == 0 || a.n % W || (x_half && prec != HISQ_F16)) return cudaErrorInvalidValue;
+    // one wave of 4 blocks per SM, two chunks a pass
+    const dim3 grid = bundle_grid(a.len, a.n / W, 4);
+    if (x_half)
+        update_px_b_kernel<__half, true><<<grid, kThreads, 0, s>>>(a, x, (const uint4*)r, (uint4*)p);
+    else
+        HISQ_BUNDLE_SWITCH(prec, (update_px_b_kernel<S, false><<<grid, kThreads, 0, s>>>(
+                                     a, x, (const uint4*)r, (uint4*)p)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_accum_solution_bundle(const BlasArgs& a, int prec, double2* x_hi, void* x_lo, int vh,
-                                         cudaStream_t s) {
+                                         bool x_half, cudaStream_t s) {
     const int W = bundle_width(prec);
-    if (W == 0 || a.n % W) return cudaErrorInvalidValue;
-    if (W == 2)
-        accum_b_kernel<2><<<bundle_grid(a.len, a.n / W), kThreads, 0, s>>>(a, x_hi, (float*)x_lo, vh);
+    if (W == 0 || a.n % W || (x_half && prec != HISQ_F16)) return cudaErrorInvalidValue;
+    const dim3 grid = bundle_grid(a.len, a.n / W);
+    if (x_half)
+        accum_b_kernel<4, true><<<grid, kThreads, 0, s>>>(a, x_hi, x_lo, vh);
+    else if (W == 2)
+        accum_b_kernel<2, false><<<grid, kThreads, 0, s>>>(a, x_hi, x_lo, vh);
     else
-        accum_b_kernel<4><<<bundle_grid(a.len, a.n / W), kThreads, 0, s>>>(a, x_hi, (float*)x_lo, vh);
+        accum_b_kernel<4, false><<<grid, kThreads, 0, s>>>(a, x_hi, x_lo, vh);
     return cudaGetLastError();
 }
 

@@ -121,7 +121,7 @@ namespace {
 struct GraphKey {
     int chunk;
     double mass, mu;
-    int rpt;
+    int rpt;   // the mapping and variant of the captured kernels, encoded
     bool operator<(const GraphKey& o) const {
         return std::tie(chunk, mass, mu, rpt) < std::tie(o.chunk, o.mass, o.mu, o.rpt);
     }
@@ -140,6 +140,7 @@ struct Workspace {
     double2* x_hi = nullptr;
     double2* r_hi = nullptr;
     double2* t_hi = nullptr;
+    double2* x_best = nullptr;   // the solution at the lowest FP64 residual so far
     CgScalars* cg = nullptr;
     CgScalars* cg_host = nullptr;
     double* partials = nullptr;
@@ -160,7 +161,7 @@ void free_workspace(Workspace* w) {
     for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
     for (auto& kv : w->loops) cudaGraphExecDestroy(kv.second);
     void* ptrs[] = {w->r_lo, w->p_lo, w->Ap_lo, w->x_lo, w->t_lo, w->b_hi, w->x_hi,
-                    w->r_hi, w->t_hi, w->cg, w->partials, w->counter};
+                    w->r_hi, w->t_hi, w->x_best, w->cg, w->partials, w->counter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (w->cg_host) cudaFreeHost(w->cg_host);
@@ -1105,6 +1106,7 @@ extern "C" void hisq_cg_default_params(hisq_cg_params* p) {
     // the bundle layout where n fits it (F32 / F16 even-odd solves), else AoS
     p->spinor_layout = HISQ_BUNDLE;
     p->device_loop = 1;
+    p->x_lo_half = 0;
     p->profile_kernels = 0;
 }
 
@@ -1143,6 +1145,7 @@ hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** o
     al((void**)&w->x_hi, hi);
     al((void**)&w->r_hi, hi);
     al((void**)&w->t_hi, thi);
+    al((void**)&w->x_best, hi);
     al((void**)&w->cg, sizeof(CgScalars));
     al((void**)&w->partials, sizeof(double) * kMaxRedVals * kMaxRedBlocks);
     al((void**)&w->counter, sizeof(unsigned int) * 4);
@@ -1152,7 +1155,7 @@ hisq_status get_workspace(hisq_gauge g, int n, int prec, int full, Workspace** o
     for (void* z : zero_lo)
         if (e == cudaSuccess) e = cudaMemset(z, 0, lo);
     if (e == cudaSuccess) e = cudaMemset(w->x_lo, 0, xlo);
-    double2* zero_hi[] = {w->b_hi, w->x_hi, w->r_hi, w->t_hi};
+    double2* zero_hi[] = {w->b_hi, w->x_hi, w->r_hi, w->t_hi, w->x_best};
     for (double2* z : zero_hi)
         if (e == cudaSuccess) e = cudaMemset(z, 0, hi);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&w->cg_host, sizeof(CgScalars));
@@ -1258,6 +1261,7 @@ struct Solver {
     int n, prec, full;
     bool bundle = false;       // low-precision vectors in the bundle layout
     bool profile = false;      // time the launches of each iteration (profile_kernels)
+    bool x_half = false;       // solution increment in half chunks (x_lo_half, FP16 bundle)
     DslashTune tune, tune64;   // inner (low precision) and FP64 Dslash mappings
     double mass, mu;
     double tol2;
@@ -1384,7 +1388,8 @@ struct Solver {
         if (bundle) {
             if (e == cudaSuccess) e = launch_cg_update_r_bundle(blas(), prec, w->r_lo, w->Ap_lo, s);
             if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
-            if (e == cudaSuccess) e = launch_cg_update_px_bundle(blas(), prec, w->x_lo, w->r_lo, w->p_lo, s);
+            if (e == cudaSuccess)
+                e = launch_cg_update_px_bundle(blas(), prec, w->x_lo, w->r_lo, w->p_lo, x_half, s);
         } else {
             if (e == cudaSuccess) e = launch_cg_update_r(blas(), prec, w->r_lo, w->Ap_lo, s);
             if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
@@ -1451,7 +1456,7 @@ struct Solver {
     }
 
     cudaError_t accum(cudaStream_t s) const {
-        return bundle ? launch_accum_solution_bundle(blas(), prec, w->x_hi, w->x_lo, g->g.vh, s)
+        return bundle ? launch_accum_solution_bundle(blas(), prec, w->x_hi, w->x_lo, g->g.vh, x_half, s)
                       : launch_accum_solution(blas(), prec, w->x_hi, w->x_lo, s);
     }
 
@@ -1463,6 +1468,7 @@ struct Solver {
     cudaError_t reliable_update(cudaStream_t s) const {
         cudaError_t e = accum(s);
         if (e == cudaSuccess) e = true_residual(s);
+        if (e == cudaSuccess) e = launch_keep_best(blas(), w->x_hi, w->x_best, s);
         if (e == cudaSuccess) e = rescale(0, s);
         return e;
     }
@@ -1571,7 +1577,8 @@ struct Solver {
             for (int i = 0; i < chunk; ++i) HISQ_CUDA(iterate(s));
             return HISQ_OK;
         }
-        GraphKey key{chunk, mass, mu, tune.kind * 1000 + tune.rpt * 100 + tune.minb * 10 + tune.layout};
+        GraphKey key{chunk, mass, mu,
+                     (x_half ? 1000000 : 0) + tune.kind * 1000 + tune.rpt * 100 + tune.minb * 10 + tune.layout};
         auto it = w->graphs.find(key);
         if (it == w->graphs.end()) {
             if (w->graphs.size() >= 8) {
@@ -1687,6 +1694,7 @@ struct CgRun {
         sv.mu = mu;
         sv.tol2 = tol * tol;
         sv.profile = prm.profile_kernels != 0;
+        sv.x_half = sv.bundle && sv.prec == HISQ_F16 && prm.x_lo_half != 0;
         for (int k = 0; k < 4; ++k) w->prof_us[k] = 0.0;
         w->prof_iters = 0;
         for (int k = 0; k < n; ++k) iters_k[k] = seen_restarts[k] = bad_updates[k] = 0;
@@ -1716,6 +1724,7 @@ struct CgRun {
         } else {
             HISQ_CUDA(launch_copy_residual(sv.blas(), w->b_hi, w->r_hi, sv.tol2, s));
         }
+        HISQ_CUDA(launch_keep_best(sv.blas(), w->x_hi, w->x_best, s));
         HISQ_CUDA(sv.rescale(1, s));
         HISQ_CUDA(sv.poll(s));
         update_stop();
@@ -1832,7 +1841,8 @@ struct CgRun {
     // The solve as one launch of a cached graph holding the device loop.
     hisq_status run_device_loop(cudaStream_t s) {
         const auto key = std::make_tuple(prm.check_every, sv.mass, sv.mu,
-                                         sv.tune.kind * 10000 + sv.tune.rpt * 100 + sv.tune.minb * 10 + sv.tune.layout,
+                                         (sv.x_half ? 1000000 : 0) + sv.tune.kind * 10000 + sv.tune.rpt * 100 +
+                                             sv.tune.minb * 10 + sv.tune.layout,
                                          prm.maxiter, prm.reliable_every, prm.reliable_delta, sv.tol2);
         auto it = w->loops.find(key);
         if (it == w->loops.end()) {
@@ -1877,6 +1887,17 @@ struct CgRun {
             res = fail(HISQ_EBREAKDOWN, "CG breakdown: <p, A p> <= 0 repeatedly with no FP64 progress");
         else if (res == HISQ_ENOCONV)
             fail(HISQ_ENOCONV, "CG did not converge in %d iterations", prm.maxiter);
+        // a solve that ends without converging returns, per rhs, the solution
+        // at the lowest FP64 residual it reached
+        double rr_out[kMaxRhs];
+        for (int k = 0; k < n; ++k) {
+            rr_out[k] = h.rr_true[k];
+            if (res != HISQ_OK && h.have_best[k] && !(h.rr_true[k] <= h.rr_best[k])) {
+                HISQ_CUDA(cudaMemcpyAsync(sv.hi_ptr(w->x_hi, k), sv.hi_ptr(w->x_best, k), vec_bytes,
+                                          cudaMemcpyDeviceToDevice, s));
+                rr_out[k] = h.rr_best[k];
+            }
+        }
         double2* xsrc = w->x_hi;
         if (soa) {
             HISQ_CUDA(launch_transpose_spinor(w->x_hi, w->t_hi, n, halves, g->g.vh, 0, s));
@@ -1889,7 +1910,7 @@ struct CgRun {
             memset(stats, 0, sizeof(*stats));
             for (int k = 0; k < n; ++k) {
                 stats->iters[k] = iters_k[k];
-                stats->true_rel_res[k] = h.bb[k] > 0 ? std::sqrt(h.rr_true[k] / h.bb[k]) : 0.0;
+                stats->true_rel_res[k] = h.bb[k] > 0 ? std::sqrt(rr_out[k] / h.bb[k]) : 0.0;
             }
             stats->total_iters = iter;
             stats->reliable_updates = reliable;

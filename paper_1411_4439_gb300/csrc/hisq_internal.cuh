@@ -180,6 +180,11 @@ struct CgScalars {
     int bad_updates[kMaxRhs];  // consecutive restarted updates without FP64 progress
     int iters_k[kMaxRhs];      // iteration at which rhs k converged
     double before[kMaxRhs];    // rr_true before the pending reliable update
+    // the lowest FP64 residual seen and whether the last one set it (the
+    // solution at that point is kept for a solve that ends without converging)
+    double rr_best[kMaxRhs];
+    int have_best[kMaxRhs];
+    int keep[kMaxRhs];
 };
 constexpr int kFlagBreakdown = 1;
 constexpr int kFlagNaN = 2;
@@ -335,6 +340,8 @@ cudaError_t launch_residual_norm(const BlasArgs& a, const double2* r_hi, double 
 // |b|^2 -> bb; active = (bb > 0); scale = 1
 cudaError_t launch_norm_bb(const BlasArgs& a, const double2* b, cudaStream_t s);
 // r_hi = b (x0 = 0) with the reliable-update finish (rr_true, rmax, scale)
+// x_best[k] = x[k] for the rhs whose last FP64 residual is their lowest (cg->keep)
+cudaError_t launch_keep_best(const BlasArgs& a, const double2* x, double2* x_best, cudaStream_t s);
 cudaError_t launch_copy_residual(const BlasArgs& a, const double2* b, double2* r_hi,
                                  double tol2, cudaStream_t s);
 // r_lo = scale * r_hi; p_lo = reset_p ? r_lo : p_lo * scale / scale_old;
@@ -344,12 +351,13 @@ cudaError_t launch_reliable_rescale(const BlasArgs& a, int prec, const double2* 
 
 // Bundle-layout versions (blas_bundle.cu): vectors [n / W][3][V_h] chunks of
 // 16 bytes (W rhs each); a.len = 3 V_h; x_lo is FP32 [n / W][3][V_h] chunks of
-// W complex numbers (real parts, then imaginary parts).
+// W complex numbers (real parts, then imaginary parts), or with x_half (FP16
+// storage only) half chunks laid out like the spinors.
 cudaError_t launch_cg_update_r_bundle(const BlasArgs& a, int prec, void* r, const void* Ap, cudaStream_t s);
 cudaError_t launch_cg_update_px_bundle(const BlasArgs& a, int prec, void* x, const void* r, void* p,
-                                       cudaStream_t s);
+                                       bool x_half, cudaStream_t s);
 cudaError_t launch_accum_solution_bundle(const BlasArgs& a, int prec, double2* x_hi, void* x_lo, int vh,
-                                         cudaStream_t s);
+                                         bool x_half, cudaStream_t s);
 cudaError_t launch_reliable_rescale_bundle(const BlasArgs& a, int prec, const double2* r_hi, void* r_lo,
                                            void* p_lo, int reset_p, int vh, cudaStream_t s);
 struct BundlePtrs {

@@ -138,6 +138,12 @@ __device__ __forceinline__ void finish_reliable(CgScalars* cg, const double* val
         cg->reset_p[k] = (nrm > 100.0 * iterated || cg->frozen[k]) ? 1 : 0;
         cg->rr_true[k] = nrm;
         cg->rmax[k] = mx;
+        const int better = isfinite(nrm) && (!cg->have_best[k] || nrm < cg->rr_best[k]);
+        cg->keep[k] = better;
+        if (better) {
+            cg->rr_best[k] = nrm;
+            cg->have_best[k] = 1;
+        }
         if (!isfinite(nrm)) {
             atomicOr(&cg->flags, kFlagNaN);
             cg->active[k] = 0;
