@@ -1074,7 +1074,7 @@ def run_cg_probe(args):
     bt = [torch.from_numpy(b[k]).to(dev) for k in range(args.n)]
     xt = [torch.zeros_like(t) for t in bt]
     p = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=args.reliable_every or RELIABLE_EVERY,
-                    maxiter=args.maxiter, device_loop=args.device_loop, x_lo_half=args.x_lo_half)
+                    maxiter=args.maxiter, device_loop=args.device_loop)
     for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1084,8 +1084,7 @@ def run_cg_probe(args):
             st = e.stats
         torch.cuda.synchronize()
         print(json.dumps({"workload": "cg probe", "lattice": list(Ls), "n": args.n,
-                          "reliable_every": p.reliable_every, "x_lo_half": p.x_lo_half,
-                          "iterations": st.total_iters,
+                          "reliable_every": p.reliable_every, "iterations": st.total_iters,
                           "reliable_updates": st.reliable_updates,
                           "max_true_rel_res": max(st.true_rel_res[k] for k in range(args.n)),
                           "s": time.perf_counter() - t0}), flush=True)
@@ -1119,8 +1118,6 @@ def main(argv=None):
     ap.add_argument("--maxiter", type=int, default=400, help="cg-probe: iteration cap")
     ap.add_argument("--reliable-every", type=int, default=0,
                     help="cg-probe: FP64 reliable update every K iterations (0: the headline's)")
-    ap.add_argument("--x-lo-half", type=int, choices=[0, 1], default=0,
-                    help="cg-probe: solution increment between reliable updates in half precision")
     ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
                     help="cg-probe: 1 = the whole solve as one graph launch, 0 = one launch per kernel")
     args = ap.parse_args(argv)

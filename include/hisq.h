@@ -382,11 +382,6 @@ typedef struct {
                               reliable_every multiples of check_every; else
                               the host decides after every check_every
                               iterations) (1) */
-    int x_lo_half;         /* 1: with FP16 inner storage in the bundle layout,
-                              the solution increment gathered between two
-                              reliable updates is stored in half precision
-                              (scaled like the spinors) instead of FP32; x
-                              itself stays FP64 (0) */
     int profile_kernels;   /* 1: time the four launches of every iteration
                               with CUDA events on the solve's stream and
                               report their mean durations in

@@ -89,25 +89,6 @@ __device__ __forceinline__ void xlo_put(float* b, long long i, const float2 (&v)
     }
 }
 
-// The solution increment in either storage: FP32 (xlo_get/put above) or,
-// with FP16 inner storage, half chunks laid out like the spinors.
-template <int W, bool XH>
-__device__ __forceinline__ void xinc_get(const void* b, long long i, float2 (&v)[W]) {
-    if constexpr (XH) {
-        static_assert(W == 4, "half increments come with FP16 storage");
-        Chunk<__half>::get(__ldg(reinterpret_cast<const uint4*>(b) + i), v);
-    } else {
-        xlo_get<W>(reinterpret_cast<const float*>(b), i, v);
-    }
-}
-template <int W, bool XH>
-__device__ __forceinline__ void xinc_put(void* b, long long i, const float2 (&v)[W]) {
-    if constexpr (XH)
-        reinterpret_cast<uint4*>(b)[i] = Chunk<__half>::put(v);
-    else
-        xlo_put<W>(reinterpret_cast<float*>(b), i, v);
-}
-
 // Per-rhs sums of a block (NV values per thread, value j of group blockIdx.y
 // is rhs blockIdx.y * NV + j) into the partial slots; in the last block,
 // s_vals[0 .. G * NV) holds the grid sums. Returns true in the last block.
@@ -188,8 +169,8 @@ __global__ void __launch_bounds__(kThreads, 4) update_r_b_kernel(BlasArgs a, uin
 }
 
 // x_lo += alpha p ; p = r + beta p (moving rhs), both from the old p.
-template <typename S, bool XH>
-__global__ void __launch_bounds__(kThreads, 4) update_px_b_kernel(BlasArgs a, void* x, const uint4* r, uint4* p) {
+template <typename S>
+__global__ void __launch_bounds__(kThreads, 4) update_px_b_kernel(BlasArgs a, float* x, const uint4* r, uint4* p) {
     constexpr int W = Chunk<S>::W;
     const int g = blockIdx.y;
     const long long nch = a.len;
@@ -217,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 4) update_px_b_kernel(BlasArgs a, vo
             const long long i = i0 + u * stride;
             if (i < nch) {
                 pc[u] = __ldg(p + off + i);
-                if (any_x) xinc_get<W, XH>(x, (long long)off + i, xv[u]);
+                if (any_x) xlo_get<W>(x, (long long)off + i, xv[u]);
                 if (any_p) rc[u] = __ldg(r + off + i);
             }
         }
@@ -234,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 4) update_px_b_kernel(BlasArgs a, vo
                     xv[u][l].x = fmaf(alpha[l], pv[l].x, xv[u][l].x);
                     xv[u][l].y = fmaf(alpha[l], pv[l].y, xv[u][l].y);
                 }
-                xinc_put<W, XH>(x, (long long)off + i, xv[u]);
+                xlo_put<W>(x, (long long)off + i, xv[u]);
             }
             if (any_p) {
                 float2 rv[W];
@@ -253,8 +234,8 @@ __global__ void __launch_bounds__(kThreads, 4) update_px_b_kernel(BlasArgs a, vo
 }
 
 // x_hi (FP64, [V_h][3] per rhs) += x_lo / scale ; x_lo = 0 (active rhs).
-template <int W, bool XH>
-__global__ void __launch_bounds__(kThreads) accum_b_kernel(BlasArgs a, double2* x_hi, void* x_lo, int vh) {
+template <int W>
+__global__ void __launch_bounds__(kThreads) accum_b_kernel(BlasArgs a, double2* x_hi, float* x_lo, int vh) {
     const int g = blockIdx.y;
     const long long nch = a.len;
     const size_t off = (size_t)g * nch;
@@ -273,7 +254,7 @@ __global__ void __launch_bounds__(kThreads) accum_b_kernel(BlasArgs a, double2* 
         const int c = (int)(i / vh);
         const long long h = i - (long long)c * vh;
         float2 lo[W];
-        xinc_get<W, XH>(x_lo, (long long)off + i, lo);
+        xlo_get<W>(x_lo, (long long)off + i, lo);
 #pragma unroll
         for (int l = 0; l < W; ++l) {
             if (!act[l]) continue;
@@ -284,7 +265,7 @@ __global__ void __launch_bounds__(kThreads) accum_b_kernel(BlasArgs a, double2* 
             *xp = v;
             lo[l] = make_float2(0.f, 0.f);
         }
-        xinc_put<W, XH>(x_lo, (long long)off + i, lo);
+        xlo_put<W>(x_lo, (long long)off + i, lo);
     }
 }
 
@@ -421,30 +402,23 @@ cudaError_t launch_cg_update_r_bundle(const BlasArgs& a, int prec, void* r, cons
 }
 
 cudaError_t launch_cg_update_px_bundle(const BlasArgs& a, int prec, void* x, const void* r, void* p,
-                                       bool x_half, cudaStream_t s) {
+                                       cudaStream_t s) {
     const int W = bundle_width(prec);
-    if (W == 0 || a.n % W || (x_half && prec != HISQ_F16)) return cudaErrorInvalidValue;
+    if (W == 0 || a.n % W) return cudaErrorInvalidValue;
     // one wave of 4 blocks per SM, two chunks a pass
-    const dim3 grid = bundle_grid(a.len, a.n / W, 4);
-    if (x_half)
-        update_px_b_kernel<__half, true><<<grid, kThreads, 0, s>>>(a, x, (const uint4*)r, (uint4*)p);
-    else
-        HISQ_BUNDLE_SWITCH(prec, (update_px_b_kernel<S, false><<<grid, kThreads, 0, s>>>(
-                                     a, x, (const uint4*)r, (uint4*)p)));
+    HISQ_BUNDLE_SWITCH(prec, (update_px_b_kernel<S><<<bundle_grid(a.len, a.n / W, 4), kThreads, 0, s>>>(
+                                 a, (float*)x, (const uint4*)r, (uint4*)p)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_accum_solution_bundle(const BlasArgs& a, int prec, double2* x_hi, void* x_lo, int vh,
-                                         bool x_half, cudaStream_t s) {
+                                         cudaStream_t s) {
     const int W = bundle_width(prec);
-    if (W == 0 || a.n % W || (x_half && prec != HISQ_F16)) return cudaErrorInvalidValue;
-    const dim3 grid = bundle_grid(a.len, a.n / W);
-    if (x_half)
-        accum_b_kernel<4, true><<<grid, kThreads, 0, s>>>(a, x_hi, x_lo, vh);
-    else if (W == 2)
-        accum_b_kernel<2, false><<<grid, kThreads, 0, s>>>(a, x_hi, x_lo, vh);
+    if (W == 0 || a.n % W) return cudaErrorInvalidValue;
+    if (W == 2)
+        accum_b_kernel<2><<<bundle_grid(a.len, a.n / W), kThreads, 0, s>>>(a, x_hi, (float*)x_lo, vh);
     else
-        accum_b_kernel<4, false><<<grid, kThreads, 0, s>>>(a, x_hi, x_lo, vh);
+        accum_b_kernel<4><<<bundle_grid(a.len, a.n / W), kThreads, 0, s>>>(a, x_hi, (float*)x_lo, vh);
     return cudaGetLastError();
 }
 

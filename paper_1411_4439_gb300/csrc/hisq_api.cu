@@ -1106,7 +1106,6 @@ extern "C" void hisq_cg_default_params(hisq_cg_params* p) {
     // the bundle layout where n fits it (F32 / F16 even-odd solves), else AoS
     p->spinor_layout = HISQ_BUNDLE;
     p->device_loop = 1;
-    p->x_lo_half = 0;
     p->profile_kernels = 0;
 }
 
@@ -1261,7 +1260,6 @@ struct Solver {
     int n, prec, full;
     bool bundle = false;       // low-precision vectors in the bundle layout
     bool profile = false;      // time the launches of each iteration (profile_kernels)
-    bool x_half = false;       // solution increment in half chunks (x_lo_half, FP16 bundle)
     DslashTune tune, tune64;   // inner (low precision) and FP64 Dslash mappings
     double mass, mu;
     double tol2;
@@ -1388,8 +1386,7 @@ struct Solver {
         if (bundle) {
             if (e == cudaSuccess) e = launch_cg_update_r_bundle(blas(), prec, w->r_lo, w->Ap_lo, s);
             if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
-            if (e == cudaSuccess)
-                e = launch_cg_update_px_bundle(blas(), prec, w->x_lo, w->r_lo, w->p_lo, x_half, s);
+            if (e == cudaSuccess) e = launch_cg_update_px_bundle(blas(), prec, w->x_lo, w->r_lo, w->p_lo, s);
         } else {
             if (e == cudaSuccess) e = launch_cg_update_r(blas(), prec, w->r_lo, w->Ap_lo, s);
             if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
@@ -1456,7 +1453,7 @@ struct Solver {
     }
 
     cudaError_t accum(cudaStream_t s) const {
-        return bundle ? launch_accum_solution_bundle(blas(), prec, w->x_hi, w->x_lo, g->g.vh, x_half, s)
+        return bundle ? launch_accum_solution_bundle(blas(), prec, w->x_hi, w->x_lo, g->g.vh, s)
                       : launch_accum_solution(blas(), prec, w->x_hi, w->x_lo, s);
     }
 
@@ -1577,8 +1574,7 @@ struct Solver {
             for (int i = 0; i < chunk; ++i) HISQ_CUDA(iterate(s));
             return HISQ_OK;
         }
-        GraphKey key{chunk, mass, mu,
-                     (x_half ? 1000000 : 0) + tune.kind * 1000 + tune.rpt * 100 + tune.minb * 10 + tune.layout};
+        GraphKey key{chunk, mass, mu, tune.kind * 1000 + tune.rpt * 100 + tune.minb * 10 + tune.layout};
         auto it = w->graphs.find(key);
         if (it == w->graphs.end()) {
             if (w->graphs.size() >= 8) {
@@ -1694,7 +1690,6 @@ struct CgRun {
         sv.mu = mu;
         sv.tol2 = tol * tol;
         sv.profile = prm.profile_kernels != 0;
-        sv.x_half = sv.bundle && sv.prec == HISQ_F16 && prm.x_lo_half != 0;
         for (int k = 0; k < 4; ++k) w->prof_us[k] = 0.0;
         w->prof_iters = 0;
         for (int k = 0; k < n; ++k) iters_k[k] = seen_restarts[k] = bad_updates[k] = 0;
@@ -1841,8 +1836,7 @@ struct CgRun {
     // The solve as one launch of a cached graph holding the device loop.
     hisq_status run_device_loop(cudaStream_t s) {
         const auto key = std::make_tuple(prm.check_every, sv.mass, sv.mu,
-                                         (sv.x_half ? 1000000 : 0) + sv.tune.kind * 10000 + sv.tune.rpt * 100 +
-                                             sv.tune.minb * 10 + sv.tune.layout,
+                                         sv.tune.kind * 10000 + sv.tune.rpt * 100 + sv.tune.minb * 10 + sv.tune.layout,
                                          prm.maxiter, prm.reliable_every, prm.reliable_delta, sv.tol2);
         auto it = w->loops.find(key);
         if (it == w->loops.end()) {

@@ -351,13 +351,12 @@ cudaError_t launch_reliable_rescale(const BlasArgs& a, int prec, const double2* 
 
 // Bundle-layout versions (blas_bundle.cu): vectors [n / W][3][V_h] chunks of
 // 16 bytes (W rhs each); a.len = 3 V_h; x_lo is FP32 [n / W][3][V_h] chunks of
-// W complex numbers (real parts, then imaginary parts), or with x_half (FP16
-// storage only) half chunks laid out like the spinors.
+// W complex numbers (real parts, then imaginary parts).
 cudaError_t launch_cg_update_r_bundle(const BlasArgs& a, int prec, void* r, const void* Ap, cudaStream_t s);
 cudaError_t launch_cg_update_px_bundle(const BlasArgs& a, int prec, void* x, const void* r, void* p,
-                                       bool x_half, cudaStream_t s);
+                                       cudaStream_t s);
 cudaError_t launch_accum_solution_bundle(const BlasArgs& a, int prec, double2* x_hi, void* x_lo, int vh,
-                                         bool x_half, cudaStream_t s);
+                                         cudaStream_t s);
 cudaError_t launch_reliable_rescale_bundle(const BlasArgs& a, int prec, const double2* r_hi, void* r_lo,
                                            void* p_lo, int reset_p, int vh, cudaStream_t s);
 struct BundlePtrs {

@@ -64,8 +64,7 @@ class hisq_cg_params(ctypes.Structure):
                 ("use_x0", ctypes.c_int), ("even_odd", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("rhs_per_thread", ctypes.c_int), ("spinor_layout", ctypes.c_int),
-                ("device_loop", ctypes.c_int), ("x_lo_half", ctypes.c_int),
-                ("profile_kernels", ctypes.c_int)]
+                ("device_loop", ctypes.c_int), ("profile_kernels", ctypes.c_int)]
 
 
 class hisq_cg_stats(ctypes.Structure):

@@ -347,30 +347,3 @@ def test_unconverged_solve_returns_the_solution_its_residual_reports(gpu_lib):
             assert abs(res[k] / st.true_rel_res[k] - 1.0) < 1e-6, (k, res[k], st.true_rel_res[k])
     finally:
         H.hisq_gauge_free(g)
-
-
-@pytest.mark.parametrize("mass", [0.05, 0.01])
-def test_half_precision_increment_solve_matches_oracle(gpu_lib, mass):
-    """x_lo_half: the increment gathered between reliable updates in half
-    chunks; the FP64 reliable updates keep the solution exact to tolerance."""
-    import torch
-    H = gpu_lib
-    L = (4, 6, 8, 10)
-    U, N = links(L)
-    g = load(H, L, 2, 18, 14)
-    try:
-        n = 8
-        b = gen.z2_source(L, n, seed=254)
-        bt = [torch.from_numpy(b[k]).cuda() for k in range(n)]
-        xt = [torch.empty_like(t) for t in bt]
-        for dl in (1, 0):
-            p = H.cg_params(inner_prec=2, spinor_layout=H.HISQ_BUNDLE, x_lo_half=1, device_loop=dl)
-            H.hisq_cg_solve(g, mass, 0.0, bt, xt, 1e-10, p)
-            x = np.stack([t.cpu().numpy() for t in xt])
-            A = lambda q: O.apply_Ae(U, N, q, L, mass)
-            assert np.all(O.true_relative_residual(A, x, b) <= 1e-10)
-            x_ref, _ = O.cg(A, b, tol=1e-13)
-            for k in range(n):
-                assert rel_l2(x[k], x_ref[k]) <= 1e-8, (dl, k)
-    finally:
-        H.hisq_gauge_free(g)
