@@ -553,3 +553,16 @@ def test_sixteen_bit_fixed_point_links_converge_where_ieee_half_links_fail(seed)
     assert res_fx <= 1e-10 and it_fx <= 1.3 * it_ref
     _, res_half = _mixed_cg_model(*blocks(_links_ieee_half(U), _links_ieee_half(N)), A, b, m)
     assert not res_half <= 1e-10
+
+
+def test_algorithmic_bytes_are_the_table_1_model_without_the_neighbour_rereads():
+    """Sec. 1 (Table 1) counts 16 neighbour reads and one write per rhs; read
+    once from DRAM, the input costs one read, so the minimum is that model
+    minus 15 re-reads of 6 reals per rhs. Hand values: FP32 18/14 at n = 8 is
+    8 * 32 * 4 + 12 * 8 * 4 = 1408 B, FP16 (16-bit links) 704 B."""
+    for n in (1, 2, 4, 8, 16):
+        for f_n in (18, 14):
+            assert (O.dslash_bytes_algorithmic(n, 18, f_n, 4, 4)
+                    == O.dslash_bytes_no_reuse(n, f_n, 18, 4) - n * 15 * 6 * 4)
+    assert O.dslash_bytes_algorithmic(8, 18, 14, 4, 4) == 1408
+    assert O.dslash_bytes_algorithmic(8, 18, 14, 2, 2) == 704
