@@ -167,7 +167,10 @@ enum {
  * HISQ_MAP_COMPACT a hop loop with the direction as a runtime loop (a quarter
  * of the code, one colour of the neighbours converted at a time),
  * HISQ_MAP_STAGED the neighbour chunks copied into shared memory by
- * asynchronous per-thread copies one hop ahead (two with HISQ_MAP_PIPELINED2). */
+ * asynchronous per-thread copies one hop ahead (two with HISQ_MAP_PIPELINED2;
+ * together with HISQ_MAP_COMPACT one, or three with HISQ_MAP_PIPELINED2).
+ * Defaults at 8 rhs per thread: FP16 storage STAGED | COMPACT at 4 blocks per
+ * SM, FP32 storage no flag at 3 blocks per SM. */
 hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_blocks,
                                     int flags);
 
