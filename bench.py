@@ -1054,9 +1054,10 @@ def run_dslash_probe(args):
 
 
 def run_cg_probe(args):
-    """One solve of the headline system (48^3x12, FP16 storage, n = 8, m =
-    0.0025) capped at --maxiter iterations, for launch lists and captures of
-    the solve's kernels; prints iterations and seconds."""
+    """One solve of the headline system (48^3x12, n = 8, m = 0.0025; FP16
+    storage, or --prec f32 / f64) capped at --maxiter iterations, for launch
+    lists, captures of the solve's kernels and storage comparisons; prints
+    iterations and seconds."""
     import torch
 
     import hisq_inputs as gen
@@ -1067,13 +1068,15 @@ def run_cg_probe(args):
     H.hisq.library()
     Ls = tuple(args.lattice)
     U, N = gen.hisq_links(Ls, seed=LINK_SEED)
-    g = H.hisq_gauge_load(Ls, torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev), prec=H.HISQ_F16,
-                          recon_U=18, recon_N=14)
+    prec = {"f16": H.HISQ_F16, "f32": H.HISQ_F32, "f64": H.HISQ_F64}[args.prec]
+    g = H.hisq_gauge_load(Ls, torch.from_numpy(U).to(dev), torch.from_numpy(N).to(dev), prec=prec,
+                          recon_U=18 if prec == H.HISQ_F64 else args.recon[0],
+                          recon_N=18 if prec == H.HISQ_F64 else args.recon[1])
     del U, N
     b = gen.gaussian_source(Ls, args.n, seed=SOURCE_SEED)
     bt = [torch.from_numpy(b[k]).to(dev) for k in range(args.n)]
     xt = [torch.zeros_like(t) for t in bt]
-    p = H.cg_params(inner_prec=H.HISQ_F16, reliable_every=args.reliable_every or RELIABLE_EVERY,
+    p = H.cg_params(inner_prec=prec, reliable_every=args.reliable_every or RELIABLE_EVERY,
                     maxiter=args.maxiter, device_loop=args.device_loop)
     for _ in range(2):
         torch.cuda.synchronize()
@@ -1083,7 +1086,7 @@ def run_cg_probe(args):
         except H.HisqError as e:      # HISQ_ENOCONV at the cap: the stats ride on the error
             st = e.stats
         torch.cuda.synchronize()
-        print(json.dumps({"workload": "cg probe", "lattice": list(Ls), "n": args.n,
+        print(json.dumps({"workload": "cg probe", "lattice": list(Ls), "n": args.n, "prec": args.prec,
                           "reliable_every": p.reliable_every, "iterations": st.total_iters,
                           "reliable_updates": st.reliable_updates,
                           "max_true_rel_res": max(st.true_rel_res[k] for k in range(args.n)),
