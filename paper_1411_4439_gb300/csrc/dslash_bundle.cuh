@@ -22,8 +22,18 @@
 // so one link element serves R / 2 pairs with 3 packed operands. Without PK
 // every rhs takes scalar FMAs. Accumulation is FP32 in both.
 //
-// Pipelining: the link of hop e + LD and the neighbour chunks of hop e + SD
-// (LD, SD in {0, 1}) are loaded before hop e is multiplied.
+// Hop loops (one per kernel variant):
+//   BundleHops                all 16 hops unrolled; the link of hop e + LD and
+//                             the neighbour chunks of hop e + SD (LD, SD in
+//                             {0, 1}) are loaded before hop e is multiplied;
+//   BundleHopsCompact         the direction as a runtime loop (a quarter of
+//                             the code: no instruction-fetch stalls);
+//   BundleHopsStaged          unrolled, the neighbour chunks copied into
+//                             shared memory D hops ahead by per-thread cp.async;
+//   BundleHopsCompactStaged   the compact loop with that staging (D = 1 or 3),
+//                             the default for FP16 storage.
+// Sites are visited plane by plane with the longer of z and t slow
+// (visit_site), so the neighbour chunks stay in L2 between their readers.
 #pragma once
 
 #include "dslash_impl.cuh"
