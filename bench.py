@@ -8,7 +8,8 @@ boundary folded in, all link reals stored as 16-bit fixed point, a bundle of
 n = 8 Gaussian complex sources, m = 0.0025, mu = 0, even-odd system
 (4m^2 - D_eo D_oe) x_e = b_e solved to a true relative residual of 1e-10 with
 FP16 spinor storage and FP32 arithmetic in the inner iteration, FP64
-reliable updates (true residual with FP64 links) and an FP64 solution.
+reliable updates every 150 iterations (true residual with FP64 links) and an
+FP64 solution.
 
 One step = one complete hisq_cg_solve of the bundle with the gauge field
 loaded and the sources resident in HBM. value = seconds per right-hand side
@@ -23,6 +24,9 @@ Also reported on the same JSON line:
                 (1146 flop/site/rhs) and fractions of both peaks
   fp64          the plain FP64 single-rhs GPU CG on the same system and
                 source 0 (the comparison of "mixed vs FP64"), s/rhs
+  cg_kernels    the four launches of an iteration of the same solve timed hot
+                (CUDA events around each launch, hisq_cg_params.profile_kernels)
+                against their byte minima
   configs1      the multi-rhs FP32 configuration (32^3x8, n = 8, m = 0.01)
   e2e           the same solve through the C ABI with pinned host buffers
   cpu_baseline  the FP64 numpy oracle on the host cores (bounded sample)
