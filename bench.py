@@ -466,19 +466,24 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def cg_kernel_byte_minima(vh: int, n: int) -> dict:
+    """Byte minima of the four launches of an FP16-storage CG iteration (U r18,
+    N r14 16-bit links, half spinors, FP32 solution increment), V_h sites."""
+    sp = 12 * n               # FP16 spinor bytes per site
+    xl = 24 * n               # FP32 x_lo bytes per site
+    links = 8 * (18 + 14) * 2
+    return {"dslash_t": (links + 2 * sp) * vh,            # t = D_oe p
+            "dslash_ap_alpha": (links + 3 * sp) * vh,     # Ap = 4m^2 p - D_eo t (reads p), Re<p, Ap>
+            "update_r": 3 * sp * vh,                      # r, Ap in; r out
+            "update_px": (3 * sp + 2 * xl) * vh}          # p, x_lo, r in; x_lo, p out
+
+
 def time_cg_kernels(H, torch, g, bt, params, stream, iters: int = 400) -> dict:
     """The four launches of a CG iteration of the headline solve, timed hot
     with CUDA events on the solve's stream (hisq_cg_params.profile_kernels)
     over the first `iters` iterations, against their byte minima: per site,
     FP16 spinors of 8 rhs are 96 B and the FP32 solution increment 192 B."""
-    vh = int(np.prod(L)) // 2
-    sp = 12 * NRHS            # FP16 spinor bytes per site
-    xl = 24 * NRHS            # FP32 x_lo bytes per site
-    links = 8 * (18 + 14) * 2
-    minima = {"dslash_t": (links + 2 * sp) * vh,            # t = D_oe p
-              "dslash_ap_alpha": (links + 3 * sp) * vh,     # Ap = 4m^2 p - D_eo t (reads p), Re<p, Ap>
-              "update_r": 3 * sp * vh,                      # r, Ap in; r out
-              "update_px": (3 * sp + 2 * xl) * vh}          # p, x_lo, r in; x_lo, p out
+    minima = cg_kernel_byte_minima(int(np.prod(L)) // 2, NRHS)
     p = H.cg_params(inner_prec=params.inner_prec, reliable_every=params.reliable_every,
                     spinor_layout=params.spinor_layout, maxiter=iters, profile_kernels=1)
     x = [torch.zeros_like(t) for t in bt]

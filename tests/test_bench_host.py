@@ -104,3 +104,16 @@ def test_warmup_is_clamped_to_three():
     finally:
         bench.run_reference = old
     assert seen["warmup"] == 3
+
+
+def test_cg_kernel_byte_minima_follow_the_dslash_byte_model():
+    """The first Dslash of an iteration moves the algorithmic bytes of one
+    Dslash; the second also reads p for its epilogue; the vector updates move
+    three (r) and three plus two FP32 (x/p) vectors of the bundle."""
+    from oracle import hisq_oracle as O
+    vh, n = 663552, 8
+    m = bench.cg_kernel_byte_minima(vh, n)
+    assert m["dslash_t"] == O.dslash_bytes_algorithmic(n, 18, 14, 2, 2) * vh == 467140608
+    assert m["dslash_ap_alpha"] - m["dslash_t"] == 6 * 2 * n * vh
+    assert m["update_r"] == 191102976
+    assert m["update_px"] == 445906944
