@@ -158,7 +158,8 @@ enum {
     HISQ_MAP_STAGED = 4,
     HISQ_MAP_PIPELINED = 8,
     HISQ_MAP_PIPELINED2 = 16,
-    HISQ_MAP_COMPACT = 128
+    HISQ_MAP_COMPACT = 128,
+    HISQ_MAP_TILE_XY = 256
 };
 /* On the bundle layout (rhs per thread 4 or 8, min blocks per SM of 128-thread
  * blocks 1..4) the kernel multiplies rhs pairs with packed FP32 (f32x2)
@@ -169,6 +170,10 @@ enum {
  * HISQ_MAP_STAGED the neighbour chunks copied into shared memory by
  * asynchronous per-thread copies one hop ahead (two with HISQ_MAP_PIPELINED2;
  * together with HISQ_MAP_COMPACT one, or three with HISQ_MAP_PIPELINED2).
+ * HISQ_MAP_TILE_XY the neighbours of the x and y hops read from a
+ * shared-memory tile of whole x-rows of the block's (z, t) plane (loaded while
+ * the z and t hops run; one rhs group, i.e. n equal to rhs per thread, and
+ * planes of whole 128-site runs, else the plain loop).
  * Defaults at 8 rhs per thread: FP16 storage STAGED | COMPACT at 4 blocks per
  * SM, FP32 storage no flag at 3 blocks per SM. */
 hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rhs_per_thread, int min_blocks,

@@ -97,7 +97,24 @@ __device__ __forceinline__ float2 stored_rhs(float2 v, __half) {
     return __half22float2(__floats2half2_rn(v.x, v.y));
 }
 
-template <typename S, typename LS, int RU, int RN, int R, bool PK, int LD, int SD>
+// Asynchronous 16-byte copies global -> shared (L1 bypassed).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Rows of the x/y neighbour tile of a block: the x-rows its 128 sites span
+// (at most 127 / hx + 2) and three more on each side for the y hops.
+__host__ __device__ constexpr int xy_tile_rows(int hx) { return 127 / hx + 8; }
+
+// XY: the neighbour chunks of the x and y hops come from a shared-memory tile
+// of whole x-rows of the block's (z, t) plane (set by set_tile), the z and t
+// hops are taken first, from global memory, while the tile arrives.
+template <typename S, typename LS, int RU, int RN, int R, bool PK, int LD, int SD, bool XY = false>
 struct BundleHops {
     using LC = typename Traits<LS>::C;
     static constexpr int W = Bundle<S>::W;
@@ -118,9 +135,30 @@ struct BundleHops {
     const LC* __restrict__ Nb;
     const uint4* __restrict__ in;   // this thread's first chunk row: group k0 / W
     int vh, p, q, h, hrow, x, y, z, t;
+    uint32_t tile = 0;              // XY: shared address of the tile
+    int tile_stride = 0;            // XY: sites per chunk plane of the tile
+    int tile_y0 = 0;                // XY: global y of tile row 0
     f2x (&ar)[P][3];
     f2x (&ai)[P][3];
     float2 (&acc)[R][3];
+
+    __device__ __forceinline__ void set_tile(uint32_t base, int stride, int y0) {
+        tile = base;
+        tile_stride = stride;
+        tile_y0 = y0;
+    }
+
+    // hop e of the S-th step: the natural order, or z, t, x, y with XY
+    template <int ST>
+    __host__ __device__ static constexpr int hop_of() {
+        if constexpr (!XY) {
+            return ST;
+        } else {
+            constexpr int D = ST >> 2;
+            constexpr int MU = D == 0 ? 2 : D == 1 ? 3 : D == 2 ? 0 : 1;
+            return (MU << 2) | (ST & 3);
+        }
+    }
 
     __device__ __forceinline__ BundleHops(const DslashArgs& args, int h_, int k0, f2x (&ar_)[P][3],
                                           f2x (&ai_)[P][3], float2 (&acc_)[R][3])
@@ -171,11 +209,38 @@ struct BundleHops {
 
     template <int E>
     __device__ __forceinline__ void issue_spin(Raw& b) const {
-        const int hn = neighbour<E>();
+        constexpr int MU = E >> 2;
+        if constexpr (XY && MU <= 1) {
+            // tile site of the neighbour: its row relative to tile row 0, and
+            // its half-index column (x hops move along the row, y hops keep it)
+            constexpr int HOP = E & 3;
+            constexpr int D = HOP == 0 ? 1 : HOP == 1 ? -1 : HOP == 2 ? 3 : -3;
+            const int Ly = a.g.L[1];
+            int row, col;
+            if constexpr (MU == 0) {
+                row = y;
+                col = wrap(x + D, a.g.L[0]) >> 1;
+            } else {
+                row = wrap(y + D, Ly);
+                col = h - hrow;
+            }
+            const int ts = wrap(row - tile_y0, Ly) * a.g.hx + col;
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int g = 0; g < NG; ++g) b.v[c][g] = __ldg(in + (size_t)(g * 3 + c) * vh + hn);
+                for (int g = 0; g < NG; ++g) {
+                    const uint32_t ad = tile + (uint32_t)((c * NG + g) * tile_stride + ts) * 16u;
+                    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                                 : "=r"(b.v[c][g].x), "=r"(b.v[c][g].y), "=r"(b.v[c][g].z), "=r"(b.v[c][g].w)
+                                 : "r"(ad));
+                }
+        } else {
+            const int hn = neighbour<E>();
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int g = 0; g < NG; ++g) b.v[c][g] = __ldg(in + (size_t)(g * 3 + c) * vh + hn);
+        }
     }
 
     template <int E>
@@ -245,18 +310,23 @@ struct BundleHops {
         }
     }
 
-    template <int E>
+    template <int ST>
     __device__ __forceinline__ void step(Raw (&buf)[2]) {
-        if constexpr (E + LD < 16) issue_link<E + LD>(buf[(E + LD) & 1]);
-        if constexpr (E + SD < 16) issue_spin<E + SD>(buf[(E + SD) & 1]);
-        compute<E>(buf[E & 1]);
-        if constexpr (E + 1 < 16) step<E + 1>(buf);
+        if constexpr (ST + LD < 16) issue_link<hop_of<ST + LD>()>(buf[(ST + LD) & 1]);
+        if constexpr (XY && ST + SD == 8) {
+            // the first x hop: the tile copies have landed for every thread
+            cp_async_wait<0>();
+            __syncthreads();
+        }
+        if constexpr (ST + SD < 16) issue_spin<hop_of<ST + SD>()>(buf[(ST + SD) & 1]);
+        compute<hop_of<ST>()>(buf[ST & 1]);
+        if constexpr (ST + 1 < 16) step<ST + 1>(buf);
     }
 
     __device__ __forceinline__ void run() {
         Raw buf[2];
-        if constexpr (LD == 1) issue_link<0>(buf[0]);
-        if constexpr (SD == 1) issue_spin<0>(buf[0]);
+        if constexpr (LD == 1) issue_link<hop_of<0>()>(buf[0]);
+        if constexpr (SD == 1) issue_spin<hop_of<0>()>(buf[0]);
         step<0>(buf);
     }
 };
@@ -427,14 +497,6 @@ struct BundleHopsCompact {
 // at ((s * 3 NG + c) * T + t) * 16 bytes, T the block's thread count:
 // consecutive threads touch consecutive 16-byte words (no bank conflicts).
 // The link of the next hop is loaded into registers one hop ahead.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 template <typename S, typename LS, int RU, int RN, int R, int D>
 struct BundleHopsStaged {
@@ -834,7 +896,37 @@ __global__ void __launch_bounds__(128, MINB) dslash_bundle_kernel(const DslashAr
         for (int k = 0; k < R; ++k)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[k][c] = make_float2(0.f, 0.f);
-        if constexpr (STAGE > 10) {
+        if constexpr (STAGE == 30) {
+            // x/y neighbour tile (one rhs group, (z, t) planes of whole
+            // 128-site runs; checked by the launcher): whole x-rows of this
+            // block's plane, three rows beyond its own on each side
+            extern __shared__ __align__(16) unsigned char bundle_smem[];
+            const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(bundle_smem));
+            const int hx = a.g.hx, Ly = a.g.L[1], plane = a.g.sz;
+            const int tsmax = xy_tile_rows(hx) * hx;
+            const int v0 = v - (int)threadIdx.x;
+            const int h0 = visit_site(v0, a.g), h1 = visit_site(v0 + (int)blockDim.x - 1, a.g);
+            const int pbase = h0 - h0 % plane;
+            const int y0 = (h0 - pbase) / hx, y1 = (h1 - pbase) / hx;
+            const int ya = wrap(y0 - 3, Ly);
+            const int ts = (y1 - y0 + 7) * hx;
+            const uint4* src = reinterpret_cast<const uint4*>(a.in[0]);
+            __syncthreads();   // every thread is done with the previous tile
+            for (int st = threadIdx.x; st < ts; st += blockDim.x) {
+                const int tr = st / hx, col = st - tr * hx;
+                const int hg = pbase + ((ya + tr) % Ly) * hx + col;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int g = 0; g < NG; ++g)
+                        cp_async16(base + (uint32_t)((c * NG + g) * tsmax + st) * 16u,
+                                   src + (size_t)(g * 3 + c) * vh + hg);
+            }
+            cp_async_commit();
+            BundleHops<S, LS, RU, RN, R, PK, LD, SD, true> hops(a, h, k0, ar, ai, acc);
+            hops.set_tile(base, tsmax, ya);
+            hops.run();
+        } else if constexpr (STAGE > 10) {
             // compact hop loop with staged neighbours, D = STAGE - 10
             extern __shared__ __align__(16) unsigned char bundle_smem[];
             const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -842,7 +934,7 @@ __global__ void __launch_bounds__(128, MINB) dslash_bundle_kernel(const DslashAr
             BundleHopsCompactStaged<S, LS, RU, RN, R, STAGE - 10> hops(a, h, k0, base + 16u * tid,
                                                                        16u * blockDim.x * blockDim.y, ar, ai);
             hops.run();
-        } else if constexpr (STAGE > 0) {
+        } else if constexpr (STAGE > 0 && STAGE < 10) {
             extern __shared__ __align__(16) unsigned char bundle_smem[];
             const int tid = threadIdx.x + threadIdx.y * blockDim.x;
             const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(bundle_smem));
@@ -915,14 +1007,29 @@ cudaError_t launch_dslash_bundle(const DslashArgs& a, cudaStream_t s) {
     const int bx = 128 / G;   // 128 threads: 128 / G sites x G rhs groups
     const dim3 block(bx, G);
     auto* kern = dslash_bundle_kernel<S, LS, RU, RN, R, MINB, PK, LD, SD, EPI, COMPACT, STAGE>;
-    // staged: (D + 1) stages x 3 R / W chunks of 16 bytes per thread, D = STAGE (unrolled
-    // loop) or STAGE - 10 (compact loop)
-    constexpr int DEPTH = STAGE > 10 ? STAGE - 10 : STAGE;
-    const size_t smem = DEPTH > 0 ? (size_t)(DEPTH + 1) * 3 * (R / Bundle<S>::W) * 16 * 128 : 0;
-    static OccCache cache;   // this kernel instance's occupancy per device
     int occ = 0;
-    cudaError_t e = cached_occupancy(cache, kern, bx * G, smem, G, &occ);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    size_t smem = 0;
+    if constexpr (STAGE == 30) {
+        // the x/y tile needs one rhs group and (z, t) planes made of whole
+        // 128-site runs; otherwise the same loop without the tile
+        smem = (size_t)3 * (R / Bundle<S>::W) * xy_tile_rows(a.g.hx) * a.g.hx * 16;
+        if (G != 1 || a.g.sz % 128 != 0 || smem > 100 * 1024)
+            return launch_dslash_bundle<S, LS, RU, RN, R, MINB, PK, LD, SD, EPI, COMPACT, 0>(a, s);
+        // the tile's size follows the lattice: occupancy per call
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bx * G, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+    } else {
+        // staged: (D + 1) stages x 3 R / W chunks of 16 bytes per thread, D = STAGE
+        // (unrolled loop) or STAGE - 10 (compact loop)
+        constexpr int DEPTH = STAGE > 10 ? STAGE - 10 : STAGE;
+        smem = DEPTH > 0 ? (size_t)(DEPTH + 1) * 3 * (R / Bundle<S>::W) * 16 * 128 : 0;
+        static OccCache cache;   // this kernel instance's occupancy per device
+        e = cached_occupancy(cache, kern, bx * G, smem, G, &occ);
+        if (e != cudaSuccess) return e;
+    }
     long long nblk = ((long long)a.g.vh + bx - 1) / bx;
     const long long cap = (long long)occ * device_sm_count();
     if (nblk > cap) nblk = cap;

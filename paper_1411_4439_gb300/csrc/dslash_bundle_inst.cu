@@ -59,6 +59,9 @@ static cudaError_t bundle_by_variant(const DslashArgs& a, int rpt, int minb, int
         case 8314: return HISQ_BS(8, 3, 13);
         case 8414: return HISQ_BS(8, 4, 13);
         case 4414: return HISQ_BS(4, 4, 13);
+        // unrolled loop with the x/y neighbour tile in shared memory: kind 15
+        case 8315: return HISQ_BS(8, 3, 30);
+        case 8215: return HISQ_BS(8, 2, 30);
 #endif
         default: return cudaErrorInvalidValue;
     }

@@ -47,7 +47,7 @@ bool bundle_mapping_built(int prec, int ru, int rn, int rpt, int minb, int kind)
     switch (key) {
         case 8205: case 4305: case 4409: case 8105: case 8106: case 8206: case 4306: case 8209: case 8409: case 4309:
         case 8210: case 8310: case 4310: case 4410: case 8211: case 8311: case 8411: case 8212: case 8312:
-        case 4411: case 8313: case 8314: case 8414: case 4414:
+        case 4411: case 8313: case 8314: case 8414: case 4414: case 8315: case 8215:
             return true;
         default:
             return false;

@@ -378,11 +378,12 @@ extern "C" hisq_status hisq_set_dslash_mapping(hisq_gauge g, int rpt, int minb, 
         return fail(HISQ_EINVAL, "rhs per thread must be 0 (auto), 1, 2, 4 or 8");
     if (minb < 0 || minb > 8) return fail(HISQ_EINVAL, "min blocks per SM must be 0 (auto) .. 8");
     if (flags & ~(HISQ_MAP_PACKED | HISQ_MAP_L2_PREFETCH | HISQ_MAP_STAGED | HISQ_MAP_PIPELINED |
-                  HISQ_MAP_PIPELINED2 | HISQ_MAP_COMPACT))
+                  HISQ_MAP_PIPELINED2 | HISQ_MAP_COMPACT | HISQ_MAP_TILE_XY))
         return fail(HISQ_EINVAL, "unknown mapping flags %d", flags);
     // STAGED with PIPELINED2 selects the bundle kernel staging two hops ahead
     const int kinds = !!(flags & HISQ_MAP_PACKED) + !!(flags & HISQ_MAP_STAGED) +
-                      !!(flags & HISQ_MAP_PIPELINED) + !!(flags & HISQ_MAP_PIPELINED2) -
+                      !!(flags & HISQ_MAP_PIPELINED) + !!(flags & HISQ_MAP_PIPELINED2) +
+                      !!(flags & HISQ_MAP_TILE_XY) -
                       ((flags & HISQ_MAP_STAGED) && (flags & HISQ_MAP_PIPELINED2) ? 1 : 0);
     if (kinds > 1) return fail(HISQ_EINVAL, "mapping flags %d name more than one kernel kind", flags);
     g->tune_rpt = rpt;
@@ -484,6 +485,7 @@ int kind_of_flags(int flags) {
 }
 
 int bundle_kind_of_flags(int flags) {
+    if (flags & HISQ_MAP_TILE_XY) return KIND_BUNDLE_XY;
     if ((flags & HISQ_MAP_STAGED) && (flags & HISQ_MAP_COMPACT))
         return (flags & HISQ_MAP_PIPELINED2) ? KIND_BUNDLE_CSMEM3 : KIND_BUNDLE_CSMEM1;
     if (flags & HISQ_MAP_STAGED) return (flags & HISQ_MAP_PIPELINED2) ? KIND_BUNDLE_SMEM2 : KIND_BUNDLE_SMEM1;
@@ -493,6 +495,7 @@ int bundle_kind_of_flags(int flags) {
 }
 
 int flags_of_tune(const DslashTune& t) {
+    if (t.layout == HISQ_BUNDLE && t.kind == KIND_BUNDLE_XY) return HISQ_MAP_TILE_XY;
     if (t.layout == HISQ_BUNDLE && (t.kind == KIND_BUNDLE_SMEM1 || t.kind == KIND_BUNDLE_SMEM2))
         return HISQ_MAP_STAGED | (t.kind == KIND_BUNDLE_SMEM2 ? HISQ_MAP_PIPELINED2 : 0);
     if (t.layout == HISQ_BUNDLE && (t.kind == KIND_BUNDLE_CSMEM1 || t.kind == KIND_BUNDLE_CSMEM3))
@@ -766,7 +769,8 @@ std::vector<DslashTune> candidate_tunes(hisq_gauge g, int n, int prec, int layou
     if (layout == HISQ_BUNDLE) {
         const int ru = link_recon_u(g, prec), rn = link_recon_n(g, prec);
         const int kinds[] = {KIND_BUNDLE, KIND_BUNDLE_SPIN, KIND_BUNDLE_COMPACT, KIND_BUNDLE_COMPACT_SPIN,
-                             KIND_BUNDLE_SMEM1, KIND_BUNDLE_SMEM2, KIND_BUNDLE_CSMEM1, KIND_BUNDLE_CSMEM3};
+                             KIND_BUNDLE_SMEM1, KIND_BUNDLE_SMEM2, KIND_BUNDLE_CSMEM1, KIND_BUNDLE_CSMEM3,
+                             KIND_BUNDLE_XY};
         for (int r : {4, 8}) {
             if (n % r != 0 || n / r > 4) continue;
             for (int b = 1; b <= 4; ++b)

@@ -248,11 +248,13 @@ enum Epi : int { EPI_NONE = 0, EPI_X = 1, EPI_XY = 2 };
 // unrolled hop loop (5), also the next hop's neighbours in flight (6), the
 // compact hop loop (9), compact with the neighbours in flight (10), and the
 // neighbour chunks copied into shared memory one (11) or two (12) hops ahead,
-// and the compact loop with the chunks staged one (13) or three (14) ahead.
+// the compact loop with the chunks staged one (13) or three (14) ahead, and
+// the unrolled loop with the x/y neighbours from a shared-memory tile (15).
 enum DslashKind : int {
     KIND_REG = 0, KIND_PACKED = 1, KIND_STAGED = 2, KIND_PIPE1 = 3, KIND_PIPE2 = 4,
     KIND_BUNDLE = 5, KIND_BUNDLE_SPIN = 6, KIND_BUNDLE_COMPACT = 9, KIND_BUNDLE_COMPACT_SPIN = 10,
-    KIND_BUNDLE_SMEM1 = 11, KIND_BUNDLE_SMEM2 = 12, KIND_BUNDLE_CSMEM1 = 13, KIND_BUNDLE_CSMEM3 = 14
+    KIND_BUNDLE_SMEM1 = 11, KIND_BUNDLE_SMEM2 = 12, KIND_BUNDLE_CSMEM1 = 13, KIND_BUNDLE_CSMEM3 = 14,
+    KIND_BUNDLE_XY = 15
 };
 struct DslashTune {
     int rpt;

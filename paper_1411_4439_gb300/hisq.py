@@ -39,6 +39,7 @@ HISQ_OP_D2M_DMU2, HISQ_OP_D3M_DMU3, HISQ_OP_D4M_DMU4 = 3, 4, 5
 HISQ_MAP_PACKED, HISQ_MAP_L2_PREFETCH, HISQ_MAP_STAGED = 1, 2, 4
 HISQ_MAP_PIPELINED, HISQ_MAP_PIPELINED2 = 8, 16
 HISQ_MAP_COMPACT = 128
+HISQ_MAP_TILE_XY = 256
 
 EXPORTED = ["hisq_version", "hisq_last_error", "hisq_gauge_load", "hisq_gauge_free",
             "hisq_gauge_info", "hisq_set_dslash_mapping", "hisq_get_dslash_mapping",

@@ -348,3 +348,33 @@ def test_unconverged_solve_returns_the_solution_its_residual_reports(gpu_lib):
             assert abs(res[k] / st.true_rel_res[k] - 1.0) < 1e-6, (k, res[k], st.true_rel_res[k])
     finally:
         H.hisq_gauge_free(g)
+
+
+# lattices whose (z, t) planes are whole 128-site runs (the tile applies),
+# one of them with Lz > Lt; and one where the launcher falls back
+@pytest.mark.parametrize("L", [(16, 16, 10, 8), (8, 32, 4, 6), (16, 16, 8, 8), (4, 6, 8, 10)])
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("minb", [2, 3])
+def test_xy_tile_bundle_dslash_matches_oracle(gpu_lib, L, prec, minb):
+    """HISQ_MAP_TILE_XY: the x and y hops read a shared-memory tile of whole
+    x-rows (Eq. 3 on a bundle); n = 8 uses the tile, n = 16 (two rhs groups)
+    the plain loop; both against the oracle on both parities."""
+    import torch
+    H = gpu_lib
+    U, N = links(L)
+    g = load(H, L, prec, 18, 14)
+    try:
+        H.hisq_set_dslash_mapping(g, 8, minb, H.HISQ_MAP_TILE_XY)
+        assert H.hisq_get_dslash_mapping_ex(g, 8, prec, H.HISQ_BUNDLE) == (8, minb, H.HISQ_MAP_TILE_XY)
+        for n in (8, 16):
+            v = gen.gaussian_source(L, n, seed=260 + n)
+            b = pack(H, g, v, prec)
+            for parity in (0, 1):
+                w = torch.full_like(b, float("nan"))
+                H.hisq_dslash_ex(g, 0.0, b, w, parity, prec, H.HISQ_BUNDLE, n=n)
+                got = unpack(H, g, w, n, prec)
+                ref = O.dslash_parity(U, N, v, L, parity)
+                for k in range(n):
+                    assert rel_l2(got[k], ref[k]) < TOL[prec], (n, parity, k)
+    finally:
+        H.hisq_gauge_free(g)
