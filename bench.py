@@ -339,9 +339,12 @@ def run_gpu(args):
         e1.synchronize()
         durs.append(e0.elapsed_time(e1) / 1e3)
         # per iteration: two Dslash, update_r, update_px; per reliable update:
-        # accumulate, two FP64 Dslash, rescale; per solve: norm |b|, copy the
-        # residual, rescale
-        launches += 4 * st.total_iters + 4 * st.reliable_updates + 3
+        # accumulate, two FP64 Dslash, best-iterate copy, rescale; per solve:
+        # norm |b|, copy the residual, best-iterate copy, rescale; per chunk
+        # of check_every iterations of the device-driven loop: the decision
+        # and booking kernels
+        chunks = -(-st.total_iters // params.check_every)
+        launches += 4 * st.total_iters + 5 * st.reliable_updates + 4 + 2 * chunks
         stats_last = st
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
